@@ -1,0 +1,472 @@
+/*
+ * lgs_oracle.c -- plain, slow FP64 CPU oracle of 3D Gaussian Splatting
+ * rasterization and of the Local-GS pieces (tile-local hoisting, tight-box
+ * warp masks).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. It shares no code, header, table or
+ * constant with the CUDA path, and it must never be used as a fallback for it.
+ *
+ * Every step is written in the order and notation of the method:
+ *   Sec. II-A  : the rasterization pipeline (preprocess, duplicate + sort by
+ *                (tile, depth) keys, per-tile front-to-back blending).
+ *   Eq. (3DGS) : alpha = o * exp(-1/2 x~^T Sigma^-1 x~), conic = [[a,b],[b,c]].
+ *   Alg. 1 (baseline column): per pixel, stop when T*(1-alpha) < 1e-4,
+ *                skip alpha < 1/255 (Sec. III-C2 threshold), clamp 0.99.
+ *   Eq. (hoist transform), Sec. III-B2: V = M(Delta) [a b c ln o]^T.
+ *   Sec. III-C2/C3: tight box Cases A/B/C and the 8-bit warp mask.
+ * The paper cites standard 3DGS for projection, covariance, EWA, radius and
+ * SH colour; those steps follow the standard definitions (readings listed
+ * beside each function).
+ *
+ * Floating point: all arithmetic in double. Inputs are float32 arrays and are
+ * promoted to double on load.
+ *
+ * Parity status of each function is pinned by the CPU test-suite:
+ *   orc_preprocess   pinned (closed form single Gaussian, EWA Jacobian by
+ *                    central differences, quaternion convention, SH basis by
+ *                    quadrature orthonormality)
+ *   orc_sort         pinned (brute-force sort of emitted keys)
+ *   orc_blend        pinned (closed form, two-Gaussian composition, alpha
+ *                    stack stop rule, invariants, brute force without tiling)
+ *   orc_hoist        pinned (identity with the direct quadratic form)
+ *   orc_warp_mask    pinned (brute-force sampling of the ellipse)
+ *   orc_backward     pinned (central finite differences of orc_* forward)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* camera layout (24 doubles): W, H, fx, fy, cx, cy, R[9] (row-major,
+ * world->camera), t[3], campos[3], bg[3] */
+enum { CAM_W = 0, CAM_H, CAM_FX, CAM_FY, CAM_CX, CAM_CY, CAM_R, CAM_T = 15,
+       CAM_POS = 18, CAM_BG = 21, CAM_SIZE = 24 };
+
+/* guard thresholds (see orc_preprocess / orc_blend) */
+enum { G_RECT_PX = 0, G_RADIUS_REL, G_NEAR_REL, G_DEPTH_REL, G_DET_REL,
+       G_ALPHA_REL, G_STOP_REL, G_SIZE };
+
+/* per-Gaussian guard flag bits */
+enum { GF_RECT = 1, GF_RADIUS = 2, GF_NEAR = 4, GF_DEPTH = 8, GF_DET = 16 };
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Real spherical harmonics from their definition.                     */
+/* Y_lm = K_lm P_l^|m|(cos th) * {sqrt2 cos(m phi), 1, sqrt2 sin(|m| phi)}
+ * with the Condon-Shortley phase inside P_l^m, ordered l^2 + l + m,
+ * m = -l..l (Sloan, "Stupid Spherical Harmonics Tricks"). */
+static double factorial(int k) { double f = 1.0; for (int i = 2; i <= k; ++i) f *= i; return f; }
+
+static double assoc_legendre(int l, int m, double x) {
+    /* P_m^m = (-1)^m (2m-1)!! (1-x^2)^{m/2}; upward recurrence in l. */
+    double pmm = 1.0;
+    double s = sqrt(fmax(0.0, 1.0 - x * x));
+    for (int i = 1; i <= m; ++i) pmm *= -(2.0 * i - 1.0) * s;
+    if (l == m) return pmm;
+    double pm1 = x * (2.0 * m + 1.0) * pmm;
+    if (l == m + 1) return pm1;
+    double pll = 0.0;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        pll = ((2.0 * ll - 1.0) * x * pm1 - (ll + m - 1.0) * pmm) / (ll - m);
+        pmm = pm1;
+        pm1 = pll;
+    }
+    return pll;
+}
+
+double orc_sh_basis(int l, int m, const double dir[3]) {
+    int am = m < 0 ? -m : m;
+    double K = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * factorial(l - am) / factorial(l + am));
+    double ct = dir[2];
+    double phi = atan2(dir[1], dir[0]);
+    double P = assoc_legendre(l, am, ct);
+    if (m > 0) return sqrt(2.0) * K * cos(m * phi) * P;
+    if (m < 0) return sqrt(2.0) * K * sin(am * phi) * P;
+    return K * P;
+}
+
+/* all (deg+1)^2 basis values */
+void orc_sh_eval(int deg, const double* dir, double* out) {
+    for (int l = 0; l <= deg; ++l)
+        for (int m = -l; m <= l; ++m) out[l * l + l + m] = orc_sh_basis(l, m, dir);
+}
+
+/* ------------------------------------------------------------------ */
+/* Rotation of a unit quaternion q = (w, x, y, z). Convention pinned by a
+ * test: (cos 45, 0, 0, sin 45) rotates e_x onto e_y. */
+void orc_quat_to_rot(const double q_in[4], double R[9]) {
+    double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Sigma = R(q) diag(s^2) R(q)^T (row-major 3x3) */
+void orc_cov3d(const double s[3], const double q[4], double S[9]) {
+    double R[9];
+    orc_quat_to_rot(q, R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[i * 3 + k] * s[k] * s[k] * R[j * 3 + k];
+            S[i * 3 + j] = acc;
+        }
+}
+
+/* EWA: 2D covariance of the projected Gaussian before the low-pass term.
+ * t = camera-space mean. J is the Jacobian of (fx x/z, fy y/z) at t with x/z
+ * and y/z clamped to +-1.3 tan(fov/2) (standard 3DGS). Out: cov2d[3] =
+ * (S00, S01, S11) of J W Sigma W^T J^T. */
+void orc_ewa(const double* cam, const double t[3], const double Sig[9], double cov2d[3]) {
+    double W = cam[CAM_W], H = cam[CAM_H], fx = cam[CAM_FX], fy = cam[CAM_FY];
+    double limx = 1.3 * (W / (2.0 * fx)), limy = 1.3 * (H / (2.0 * fy));
+    double tz = t[2];
+    double txz = t[0] / tz, tyz = t[1] / tz;
+    if (txz < -limx) txz = -limx; if (txz > limx) txz = limx;
+    if (tyz < -limy) tyz = -limy; if (tyz > limy) tyz = limy;
+    double xh = txz * tz, yh = tyz * tz;
+    double J[6] = { fx / tz, 0.0, -fx * xh / (tz * tz),
+                    0.0, fy / tz, -fy * yh / (tz * tz) };
+    const double* Rw = cam + CAM_R;
+    double T[6]; /* T = J W (2x3) */
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += J[i * 3 + k] * Rw[k * 3 + j];
+            T[i * 3 + j] = acc;
+        }
+    double C[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += T[i * 3 + k] * Sig[k * 3 + l] * T[j * 3 + l];
+            C[i * 2 + j] = acc;
+        }
+    cov2d[0] = C[0];
+    cov2d[1] = C[1];
+    cov2d[2] = C[3];
+}
+
+static double frac_dist(double q) { double f = q - floor(q); return f < 0.5 ? f : 1.0 - f; }
+
+/* distance (in units of q) from q to the nearest integer k with lo <= k <= hi */
+static double int_dist_in(double q, int lo, int hi) {
+    double k = floor(q + 0.5);
+    if (k < lo) k = lo;
+    if (k > hi) k = hi;
+    return fabs(q - k);
+}
+
+/* ------------------------------------------------------------------ */
+/* Preprocess: one Gaussian per iteration, standard 3DGS semantics.
+ * Outputs (per Gaussian i):
+ *   uv[2i..]      projected mean (pixel units, pixel (i,j) sampled at (i,j))
+ *   depth[i]      camera-space z (double); depth_bits[i] = bits of (float)z
+ *   conic[3i..]   (a, b, c) of Sigma'^-1
+ *   radius[i]     ceil(3 sqrt(lambda_max)), 0 when culled
+ *   rect[4i..]    tile rect x_lo, y_lo, x_hi, y_hi (half-open)
+ *   tiles[i]      (x_hi-x_lo)*(y_hi-y_lo), 0 when culled
+ *   rgb[3i..]     max(0, SH colour + 0.5); clamped[3i..] = pre-clamp value < 0
+ *   gflags[i]     guard bits (decision within its guard band)
+ */
+void orc_preprocess(int64_t n, int sh_degree, const float* means, const float* scales,
+                    const float* quats, const float* opac, const float* sh,
+                    const double* cam, int tile_w, int tile_h, const double* guard,
+                    double* uv, double* depth, uint32_t* depth_bits, double* conic,
+                    int32_t* radius, int32_t* rect, int64_t* tiles, double* rgb,
+                    uint8_t* clamped, uint8_t* gflags) {
+    int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
+    int gx = (W + tile_w - 1) / tile_w, gy = (H + tile_h - 1) / tile_h;
+    const double* R = cam + CAM_R;
+    const double* tc = cam + CAM_T;
+    int K = (sh_degree + 1) * (sh_degree + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        uint8_t gf = 0;
+        double mu[3] = { means[3 * i], means[3 * i + 1], means[3 * i + 2] };
+        double t[3];
+        for (int r = 0; r < 3; ++r)
+            t[r] = ((R[r * 3 + 0] * mu[0] + R[r * 3 + 1] * mu[1]) + R[r * 3 + 2] * mu[2]) + tc[r];
+        radius[i] = 0; tiles[i] = 0;
+        rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
+        uv[2 * i] = uv[2 * i + 1] = 0.0;
+        depth[i] = t[2];
+        {
+            float zf = (float)t[2];
+            memcpy(&depth_bits[i], &zf, 4);
+            /* guard: fp64 depth close to a float32 rounding midpoint */
+            double lo = nextafterf(zf, -INFINITY), hi = nextafterf(zf, INFINITY);
+            double mid = t[2] >= (double)zf ? 0.5 * ((double)zf + hi) : 0.5 * ((double)zf + lo);
+            if (fabs(t[2] - mid) < guard[G_DEPTH_REL] * fabs(t[2])) gf |= GF_DEPTH;
+        }
+        conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0.0;
+        rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0.0;
+        clamped[3 * i] = clamped[3 * i + 1] = clamped[3 * i + 2] = 0;
+        if (fabs(t[2] - 0.2) < guard[G_NEAR_REL] * 0.2) gf |= GF_NEAR;
+        if (t[2] <= 0.2) { gflags[i] = gf; continue; }          /* near-plane cull */
+        double s[3] = { scales[3 * i], scales[3 * i + 1], scales[3 * i + 2] };
+        double q[4] = { quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3] };
+        double Sig[9], cv[3];
+        orc_cov3d(s, q, Sig);
+        orc_ewa(cam, t, Sig, cv);
+        cv[0] += 0.3; cv[2] += 0.3;                              /* low-pass dilation */
+        double det = cv[0] * cv[2] - cv[1] * cv[1];
+        if (det < guard[G_DET_REL] * cv[0] * cv[2]) gf |= GF_DET;
+        if (det <= 0.0) { gflags[i] = gf; continue; }
+        double a = cv[2] / det, b = -cv[1] / det, c = cv[0] / det;
+        double mid = 0.5 * (cv[0] + cv[2]);
+        double lam1 = mid + sqrt(fmax(0.1, mid * mid - det));
+        double r3 = 3.0 * sqrt(lam1);
+        double rr = ceil(r3);
+        if (frac_dist(r3) < guard[G_RADIUS_REL] * r3) gf |= GF_RADIUS;
+        double u = cam[CAM_FX] * (t[0] / t[2]) + cam[CAM_CX];
+        double v = cam[CAM_FY] * (t[1] / t[2]) + cam[CAM_CY];
+        double qx0 = (u - rr) / tile_w, qx1 = (u + rr + tile_w - 1) / tile_w;
+        double qy0 = (v - rr) / tile_h, qy1 = (v + rr + tile_h - 1) / tile_h;
+        int x0 = (int)fmin(gx, fmax(0.0, floor(qx0)));
+        int x1 = (int)fmin(gx, fmax(0.0, floor(qx1)));
+        int y0 = (int)fmin(gy, fmax(0.0, floor(qy0)));
+        int y1 = (int)fmin(gy, fmax(0.0, floor(qy1)));
+        double gpx = guard[G_RECT_PX];
+        if (int_dist_in(qx0, 1, gx) * tile_w < gpx || int_dist_in(qx1, 1, gx) * tile_w < gpx ||
+            int_dist_in(qy0, 1, gy) * tile_h < gpx || int_dist_in(qy1, 1, gy) * tile_h < gpx)
+            gf |= GF_RECT;
+        gflags[i] = gf;
+        int64_t area = (int64_t)(x1 - x0) * (int64_t)(y1 - y0);
+        if (area == 0) continue;
+        /* colour from SH in the view direction */
+        double d[3] = { mu[0] - cam[CAM_POS], mu[1] - cam[CAM_POS + 1], mu[2] - cam[CAM_POS + 2] };
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] /= dn; d[1] /= dn; d[2] /= dn;
+        double Y[16];
+        orc_sh_eval(sh_degree, d, Y);
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += Y[k] * sh[(i * K + k) * 3 + ch];
+            acc += 0.5;
+            clamped[3 * i + ch] = acc < 0.0;
+            rgb[3 * i + ch] = acc < 0.0 ? 0.0 : acc;
+        }
+        uv[2 * i] = u; uv[2 * i + 1] = v;
+        conic[3 * i] = a; conic[3 * i + 1] = b; conic[3 * i + 2] = c;
+        radius[i] = (int32_t)rr;
+        rect[4 * i] = x0; rect[4 * i + 1] = y0; rect[4 * i + 2] = x1; rect[4 * i + 3] = y1;
+        tiles[i] = area;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Duplicate + sort (Sec. II-A): key = (tile_id << 32) | bits(float depth),
+ * emitted in Gaussian order, tiles row-major inside each rect; sorted
+ * ascending by key with ties kept in emission order (stable sort).
+ * tile_id = tile_offset + ty*gx + tx. ranges[2t..] = [first, last+1) or (0,0). */
+typedef struct { uint64_t key; int64_t pos; uint32_t val; } orc_kv;
+
+static int kv_cmp(const void* pa, const void* pb) {
+    const orc_kv* a = (const orc_kv*)pa; const orc_kv* b = (const orc_kv*)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->pos < b->pos ? -1 : (a->pos > b->pos);
+}
+
+int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_offset,
+                 const int32_t* rect, const int64_t* tiles, const uint32_t* depth_bits,
+                 int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+    int64_t K = 0;
+    for (int64_t i = 0; i < n; ++i) K += tiles[i];
+    if (K > capacity) return -K;
+    orc_kv* kv = (orc_kv*)malloc(sizeof(orc_kv) * (size_t)(K > 0 ? K : 1));
+    int64_t p = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (tiles[i] == 0) continue;
+        for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
+            for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
+                uint64_t tid = (uint64_t)(tile_offset + (int64_t)ty * gx + tx);
+                kv[p].key = (tid << 32) | depth_bits[i];
+                kv[p].val = (uint32_t)i + val_offset;
+                kv[p].pos = p;
+                ++p;
+            }
+    }
+    qsort(kv, (size_t)K, sizeof(orc_kv), kv_cmp);
+    int64_t nt = (int64_t)gx * gy;
+    for (int64_t t = 0; t < 2 * nt; ++t) ranges[t] = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        keys[k] = kv[k].key;
+        vals[k] = kv[k].val;
+        int64_t t = (int64_t)(kv[k].key >> 32) - tile_offset;
+        if (k == 0 || (kv[k - 1].key >> 32) != (kv[k].key >> 32)) ranges[2 * t] = (uint32_t)k;
+        ranges[2 * t + 1] = (uint32_t)(k + 1);
+    }
+    free(kv);
+    return K;
+}
+
+/* ------------------------------------------------------------------ */
+/* Front-to-back blending, Alg. 1 baseline column, one pixel at a time.
+ * For each pixel (px, py) of tile t and each Gaussian k of its list in order:
+ *   d = (u_k - px, v_k - py); p = -1/2 d^T Q d
+ *   alpha = min(0.99, o exp(p)); skip if alpha < 1/255
+ *   test_T = T (1 - alpha); stop (without blending) if test_T < 1e-4
+ *   C += rgb alpha T; T = test_T; last = position of k in the list + 1
+ * out: rgb [3,H,W] = C + T bg; final_T [H,W]; n_contrib [H,W] = last.
+ * pguard [H,W]: 1 if an alpha or stop decision on the pixel's path lay inside
+ * its relative guard band. stop_pos [H,W] (optional): list position (1-based)
+ * of the Gaussian whose test_T fell below 1e-4, 0 if the pixel never stopped.
+ * n_useful [H,W] (optional): blended Gaussians. vals index the per-Gaussian
+ * arrays directly. */
+void orc_blend(int W, int H, int tile_w, int tile_h, const double* bg,
+               const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
+               const double* uv, const double* conic, const float* opac, const double* rgb,
+               const double* guard, double* out_rgb, double* final_T, uint32_t* n_contrib,
+               uint8_t* pguard, uint32_t* stop_pos, uint32_t* n_useful) {
+    int gx = (W + tile_w - 1) / tile_w;
+    const double a_min = 1.0 / 255.0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+        int px = (int)(pix % W), py = (int)(pix / W);
+        int64_t tile = tile_offset + (int64_t)(py / tile_h) * gx + px / tile_w;
+        uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+        double T = 1.0, C[3] = { 0, 0, 0 };
+        uint32_t last = 0, stop = 0, useful = 0;
+        uint8_t g = 0;
+        for (uint32_t k = s; k < e; ++k) {
+            uint32_t id = vals[k];
+            double dx = uv[2 * id] - px, dy = uv[2 * id + 1] - py;
+            double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2];
+            double p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+            double al = (double)opac[id] * exp(p);
+            if (al > 0.99) al = 0.99;
+            if (fabs(al - a_min) < guard[G_ALPHA_REL] * a_min) g = 1;
+            if (al < a_min) continue;
+            double test_T = T * (1.0 - al);
+            if (fabs(test_T - 1e-4) < guard[G_STOP_REL] * 1e-4) g = 1;
+            if (test_T < 1e-4) { stop = k - s + 1; break; }
+            ++useful;
+            for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * id + ch] * al * T;
+            T = test_T;
+            last = k - s + 1;
+        }
+        for (int ch = 0; ch < 3; ++ch) out_rgb[(int64_t)ch * W * H + pix] = C[ch] + T * bg[ch];
+        final_T[pix] = T;
+        n_contrib[pix] = last;
+        pguard[pix] = g;
+        if (stop_pos) stop_pos[pix] = stop;
+        if (n_useful) n_useful[pix] = useful;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Hoist transform (Eq. hoist transform, Sec. III-B2): with the tile-local
+ * displacement Delta = mu - T_origin,
+ *   [A B C D E F]^T = M(Delta) [a b c ln o]^T
+ * so that ln alpha = A x'^2 + B x'y' + C y'^2 + D x' + E y' + F for a pixel at
+ * tile-local x' = x - T_origin. */
+void orc_hoist(double a, double b, double c, double o, double dx, double dy, double V[6]) {
+    double lno = log(o);
+    V[0] = -0.5 * a;
+    V[1] = -1.0 * b;
+    V[2] = -0.5 * c;
+    V[3] = dx * a + dy * b;
+    V[4] = dx * b + dy * c;
+    V[5] = -0.5 * dx * dx * a - dx * dy * b - 0.5 * dy * dy * c + 1.0 * lno;
+}
+
+/* Tight box and warp mask (Sec. III-C2, III-C3) for one Gaussian and one
+ * tile column of width tile_w starting at pixel column X0, rows Y0..Y0+tile_h-1
+ * split into n_warps strips of tile_h/n_warps rows.
+ *   tau = 2 ln(255 o); ellipse a x~^2 + 2b x~y~ + c y~^2 = tau
+ *   x~ in [X0 - mu_x, X0 + tile_w - 1 - mu_x]; d_y = sqrt(a tau/(ac - b^2))
+ *   upper bound: Case A (-b d_y < a x~0) -> root at x~0; Case B (-b d_y > a x~1)
+ *   -> root at x~1; Case C -> d_y. Lower bound symmetric (peak at +b d_y / a).
+ * Reading: the strip is first intersected with the ellipse's x-extent
+ * |x~| <= sqrt(c tau/(ac - b^2)); a strip outside it gives mask 0, and the
+ * clamp keeps the square roots real. Returns the warp bit mask. */
+uint32_t orc_warp_mask(double a, double b, double c, double o, double mux, double muy,
+                       int X0, int Y0, int tile_w, int tile_h, int n_warps) {
+    double tau = 2.0 * log(255.0 * o);
+    if (!(tau > 0.0)) return 0u;
+    double det = a * c - b * b;
+    double xr = sqrt(c * tau / det);
+    double x0 = X0 - mux, x1 = X0 + tile_w - 1 - mux;
+    if (x1 < -xr || x0 > xr) return 0u;
+    if (x0 < -xr) x0 = -xr;
+    if (x1 > xr) x1 = xr;
+    double dy = sqrt(a * tau / det);
+    double ymax, ymin;
+    if (-b * dy < a * x0)      ymax = (-b * x0 + sqrt(fmax(0.0, c * tau - det * x0 * x0))) / c;
+    else if (-b * dy > a * x1) ymax = (-b * x1 + sqrt(fmax(0.0, c * tau - det * x1 * x1))) / c;
+    else                       ymax = dy;
+    if (b * dy < a * x0)       ymin = (-b * x0 - sqrt(fmax(0.0, c * tau - det * x0 * x0))) / c;
+    else if (b * dy > a * x1)  ymin = (-b * x1 - sqrt(fmax(0.0, c * tau - det * x1 * x1))) / c;
+    else                       ymin = -dy;
+    double ylo = muy + ymin, yhi = muy + ymax;
+    int ys = (int)fmax((double)Y0, ceil(ylo));
+    int ye = (int)fmin((double)(Y0 + tile_h - 1), floor(yhi));
+    if (ys > ye) return 0u;
+    int rows = tile_h / n_warps;
+    int ws = (ys - Y0) / rows, we = (ye - Y0) / rows;
+    return ((1u << (we - ws + 1)) - 1u) << ws;
+}
+
+/* Work of the Local-GS schedule in pixel-Gaussian pairs: for every tile and
+ * every warp strip, the Gaussians of the tile list whose mask bit for the
+ * strip is set, counted up to and including the first one after which every
+ * pixel of the strip has stopped (or the end of the list); times the pixels
+ * of the strip (the lanes of a warp). n_contrib/stop positions come from the
+ * blend above: a pixel has stopped once the list position passes its stop
+ * position. stop_pos[pix] = list position (1-based) of the Gaussian that
+ * triggered the stop, or 0 when the pixel never stopped. */
+int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
+                          const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
+                          const double* uv, const double* conic, const float* opac,
+                          const uint32_t* stop_pos) {
+    int gx = (W + tile_w - 1) / tile_w, gy = (H + tile_h - 1) / tile_h;
+    int rows = tile_h / n_warps;
+    int64_t total = 0;
+    for (int ty = 0; ty < gy; ++ty)
+        for (int tx = 0; tx < gx; ++tx) {
+            int64_t tile = tile_offset + (int64_t)ty * gx + tx;
+            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+            int X0 = tx * tile_w, Y0 = ty * tile_h;
+            for (int w = 0; w < n_warps; ++w) {
+                /* stop position of the warp = max over its pixels (0 = never) */
+                uint32_t wstop = 0;
+                int never = 0;
+                for (int r = 0; r < rows; ++r)
+                    for (int cc = 0; cc < tile_w; ++cc) {
+                        int px = X0 + cc, py = Y0 + w * rows + r;
+                        if (px >= W || py >= H) continue;      /* out-of-image lanes are done */
+                        uint32_t sp = stop_pos[(int64_t)py * W + px];
+                        if (sp == 0) never = 1;
+                        else if (sp > wstop) wstop = sp;
+                    }
+                for (uint32_t k = s; k < e; ++k) {
+                    uint32_t pos = k - s + 1;
+                    if (!never && pos > wstop) break;
+                    uint32_t id = vals[k];
+                    uint32_t m = orc_warp_mask(conic[3 * id], conic[3 * id + 1], conic[3 * id + 2],
+                                               opac[id], uv[2 * id], uv[2 * id + 1], X0, Y0,
+                                               tile_w, tile_h, n_warps);
+                    if (m & (1u << w)) total += (int64_t)rows * tile_w;
+                }
+            }
+        }
+    return total;
+}
