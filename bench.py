@@ -1,0 +1,355 @@
+"""Benchmark of the Local-GS rasterization path on one GB300 (or N replicas).
+
+Workload (outdoor scene): 500,000 Gaussians FP32 with SH degree 3 drawn from 64
+anisotropic clusters plus a 10 % background shell at radius 10, seen by 8
+orbit cameras at 1264x832 (16x16 tiles). One step renders all 8 views through
+the whole hot path: preprocess -> scan/emit/radix sort/ranges -> render, in
+one batched launch per stage. ``value`` is frames (views) per second over all
+ranks; Mpix/s, the plain tiled rasterizer on the same inputs, per-stage times
+and the roofline of the dominant kernel are reported beside it.
+
+Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
+launching stream; L2 is flushed (256 MB write) between steps, outside the
+events. Under torchrun each rank renders its own 8 views (replicas: no data
+exchange), and the time is the maximum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+reference arm of this project: there is no other implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "outdoor-500k-sh3-8x1264x832"
+METRIC = "frames/s (Local-GS fwd, 8 views of 1264x832, 500k Gaussians SH3)"
+CROP = (158, 104)          # 1/64 of a 1264x832 view: one oracle sample
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_crops(scene, cams, n_crops, seed=7):
+    import oracle
+    from paper_2606_16566_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    t0 = time.perf_counter()
+    for _ in range(n_crops):
+        x0 = int(rng.integers(0, (W - CROP[0]) // 16)) * 16
+        y0 = int(rng.integers(0, (H - CROP[1]) // 16)) * 16
+        oracle.render(scene, scenes.crop_camera(cam, x0, y0, *CROP))
+    return time.perf_counter() - t0
+
+
+def crop_fraction(cams):
+    return CROP[0] * CROP[1] / (cams[0]["width"] * cams[0]["height"])
+
+
+def cpu_baseline(scene, cams, budget_s=15.0):
+    import oracle
+    t1 = oracle_crops(scene, cams, 1)
+    n = max(1, min(64, int(budget_s / max(t1, 1e-3))))
+    t = oracle_crops(scene, cams, n, seed=11)
+    fps = n * crop_fraction(cams) / t
+    return {"value": fps, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} random {CROP[0]}x{CROP[1]} crops of view 0 (each 1/64 of a frame; full "
+                      f"preprocess+sort of all 500k Gaussians per crop), rate scaled by pixel fraction"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2606_16566_gb300 import scenes
+    import oracle
+    scene, cams = scenes.outdoor()
+    for _ in range(args.warmup):
+        oracle_crops(scene, cams, 1, seed=3)
+    t = oracle_crops(scene, cams, args.steps, seed=5)
+    fps = args.steps * crop_fraction(cams) / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{CROP[0]}x{CROP[1]} crop per step"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"one random {CROP[0]}x{CROP[1]} crop (1/64 frame) of view 0 per step, "
+                                   "rate scaled by pixel fraction"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+class Pipeline:
+    """Preallocated buffers for repeated batched frames through the C ABI."""
+
+    def __init__(self, g, cams, tile, capacity):
+        import torch
+        from paper_2606_16566_gb300 import lgs
+        self.lgs, self.torch = lgs, torch
+        self.g, self.cams, self.tile = g, cams, tile
+        self.n = g["means"].shape[0]
+        self.m = self.n * len(cams)
+        self.carr = lgs.cameras(cams)
+        dev = g["means"].device
+        self.status = lgs.new_status(dev)
+        self.pre = lgs.PreOut.empty(self.m, dev)
+        self.capacity = capacity
+        self.keys = torch.empty(capacity, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
+        self.ranges = torch.empty((lgs.n_tiles(cams, lgs.config(tile)), 2), dtype=torch.int32, device=dev)
+        self.ws = torch.empty(lgs.sort_workspace_size(self.m, capacity), dtype=torch.uint8, device=dev)
+        P = lgs.n_pixels(cams)
+        self.rgb = torch.empty(3 * P, dtype=torch.float32, device=dev)
+        self.T = torch.empty(P, dtype=torch.float32, device=dev)
+        self.nc = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def stage_pre(self, cfg):
+        self.status.zero_()
+        self.lgs.preprocess(self.g, self.cams, cfg, out=self.pre, status=self.status)
+
+    def stage_sort(self, cfg):
+        self.lgs.sort(self.pre, self.n, self.cams, cfg, self.capacity, self.keys, self.vals, self.ranges,
+                      self.ws, self.status)
+
+    def stage_render(self, cfg):
+        self.lgs.render_fwd(self.pre, self.vals, self.ranges, self.cams, cfg, self.rgb, self.T, self.nc,
+                            self.status)
+
+    def step(self, cfg):
+        self.stage_pre(cfg)
+        self.stage_sort(cfg)
+        self.stage_render(cfg)
+
+    def launches(self):
+        from math import ceil
+        nt = self.ranges.shape[0]
+        bits = 0
+        while (1 << bits) < nt:
+            bits += 1
+        passes = ceil((32 + bits) / 8)
+        return 1 + 3 + 1 + 3 * passes + 1 + 1
+
+
+def time_steps(pipe, cfg, steps, flush):
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        e = ev[i]
+        e[0].record()
+        pipe.stage_pre(cfg)
+        e[1].record()
+        pipe.stage_sort(cfg)
+        e[2].record()
+        pipe.stage_render(cfg)
+        e[3].record()
+    torch.cuda.synchronize()
+    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in ev])
+    return stage  # [steps, 3] ms
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2606_16566_gb300 import lgs, scenes
+    from paper_2606_16566_gb300 import _lib as L
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    scene, cams = scenes.outdoor()
+    g = lgs.to_device(scene, dev)
+    cfg_l = lgs.config(tile, "localgs")
+    cfg_p = lgs.config(tile, "plain")
+
+    # discover K and size the instance buffers once (outside the timed region)
+    probe = lgs.render(g, cams, tile=tile)
+    K = probe["K"]
+    pipe = Pipeline(g, cams, tile, int(K * 1.05) + 1024)
+    del probe
+    # schedule work of the Local-GS render (pixel-Gaussian pairs), counted once
+    pipe.step(lgs.config(tile, "localgs", flags=L.FLAG_COUNT))
+    st = lgs.read_status(pipe.status)
+    pairs_l = int(st[L.ST_PAIRS])
+    pipe.step(lgs.config(tile, "plain", flags=L.FLAG_COUNT))
+    pairs_p = int(lgs.read_status(pipe.status)[L.ST_PAIRS])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        pipe.step(cfg_l)
+        pipe.step(cfg_p)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with Clocks(dev.index) as clk:
+        st_l = time_steps(pipe, cfg_l, args.steps, flush)
+        st_p = time_steps(pipe, cfg_p, args.steps, flush)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_l = float(st_l.sum(1).mean())
+    ms_p = float(st_p.sum(1).mean())
+    if world > 1:
+        t = torch.tensor([ms_l, ms_p], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_l, ms_p = t.tolist()
+    views = len(cams)
+    P = lgs.n_pixels(cams)
+    fps = world * views / (ms_l * 1e-3)
+    fps_p = world * views / (ms_p * 1e-3)
+    stage_ms = st_l.mean(0)
+    render_ms = float(stage_ms[2])
+    sm_max = 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at max SM clock
+    flops = pairs_l * 19.0
+    achieved = flops / (render_ms * 1e-3) / 1e12
+
+    # end to end: host scene -> device, pipeline, image -> host, every step
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).pin_memory() for k in g}
+        out_h = torch.empty(pipe.rgb.numel(), dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values())
+        d2h = out_h.numel() * 4
+        for _ in range(2):
+            for k in g:
+                g[k].copy_(host[k], non_blocking=True)
+            pipe.step(cfg_l)
+            out_h.copy_(pipe.rgb, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(5, args.steps // 2)
+        e0.record()
+        for _ in range(n_e2e):
+            for k in g:
+                g[k].copy_(host[k], non_blocking=True)
+            pipe.step(cfg_l)
+            out_h.copy_(pipe.rgb, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / n_e2e
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = t.item()
+        e2e = {"value": world * views / (ms_e2e * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n, "tile": args.tile,
+                   "instances_K": K, "l2": "flushed between steps (256 MB write, outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "mpix_s": world * views * (P / views) / 1e6 / (ms_l * 1e-3),
+        "stage_ms": {"preprocess": float(stage_ms[0]), "sort": float(stage_ms[1]), "render": render_ms},
+        "plain": {"frames_s": fps_p, "mpix_s": world * P / 1e6 / (ms_p * 1e-3), "ms_per_step": ms_p,
+                  "render_ms": float(st_p.mean(0)[2]), "pairs": pairs_p},
+        "render_speedup_vs_plain": float(st_p.mean(0)[2]) / render_ms,
+        "roofline": {"bound": "alu", "kernel": "render_localgs", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "work": f"{pairs_l} pixel-Gaussian pairs x 19 FP32 flops",
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "gpu_launches": pipe.launches() * args.steps * 2,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cams)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * lgs.h -- C ABI of the GB300 (sm_103a) Local-GS 3D Gaussian Splatting
+ * rasterizer.
+ *
+ * The library renders N anisotropic 3D Gaussians (mean, scale, rotation,
+ * opacity, SH colour; Local-GS Sec. II-A) seen by one or more pinhole cameras
+ * into an RGB image, its final transmittance T and the per-pixel contributor
+ * count, through the three stages of the 3DGS rasterization pipeline
+ * (Sec. II-A, Fig. 2): preprocess, duplicate + sort by (tile, depth) keys,
+ * per-tile render. The render stage implements Local-GS (Sec. III): tile-local
+ * parameter hoisting (Sec. III-B, Eq. hoist transform), warp-level culling with
+ * the tight box and 8-bit warp mask (Sec. III-C), and warp-coherent blending
+ * (Sec. III-D, Alg. 1 right column) -- alongside a plain per-pixel tiled
+ * kernel (Alg. 1 left column) for comparison. The backward entry point is the
+ * adjoint of the same forward map.
+ *
+ * Conventions (all entry points):
+ *  - Every buffer is caller-owned. The library never allocates or frees memory;
+ *    scratch comes from a caller-provided workspace whose size a *_workspace_size
+ *    query returns.
+ *  - Device pointers are CUDA device addresses on the current device; `stream`
+ *    is a cudaStream_t (NULL = legacy default stream). All work is enqueued
+ *    asynchronously on that stream; no entry point synchronises except
+ *    lgs_read_status. Calls are therefore capturable in a CUDA graph.
+ *  - Host-checkable errors (NULL pointers, bad sizes, misalignment, unsupported
+ *    tile shapes or SH degrees) return a non-zero lgs_status before anything is
+ *    enqueued. Errors detected on the device (instance capacity exceeded,
+ *    bounded waits that gave up) are recorded in the caller's device status
+ *    buffer `d_status` (LGS_STATUS_WORDS int64 words, zeroed by the caller
+ *    before the first call of a frame) and read back with lgs_read_status.
+ *  - Arrays loaded as float4 (marked "16-B aligned") must start on a 16-byte
+ *    boundary, otherwise LGS_ERR_ALIGN.
+ *  - No C++ exception crosses the ABI. The library holds no mutable global
+ *    state.
+ *
+ * Multi-view batches: n_views cameras (1..LGS_MAX_VIEWS) are processed in one
+ * call. Per-(view, Gaussian) arrays are view-major, index v*N + i. Tile ids are
+ * global across the batch: tile_id = (tiles of views 0..v-1) + ty*gx + tx.
+ * Per-pixel outputs are concatenated per view: view v's image starts at pixel
+ * offset P_v = sum_{u<v} W_u*H_u; rgb is channel-major within a view
+ * (rgb[3*P_v + c*H_v*W_v + y*W_v + x]); final_T and n_contrib at P_v + y*W_v + x.
+ */
+#ifndef LGS_H
+#define LGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lgs_status;
+#define LGS_OK 0
+#define LGS_ERR_ARG 1          /* NULL pointer, negative or inconsistent size */
+#define LGS_ERR_ALIGN 2        /* a float4-loaded array is not 16-byte aligned */
+#define LGS_ERR_UNSUPPORTED 3  /* tile shape, SH degree or view count not supported */
+#define LGS_ERR_CAPACITY 4     /* instance capacity too small (device: needed K in detail) */
+#define LGS_ERR_NONFINITE 5    /* reserved: non-finite inputs are counted, not fatal */
+#define LGS_ERR_TIMEOUT 6      /* a bounded device-side wait gave up */
+#define LGS_ERR_CUDA 7         /* a CUDA launch failed (detail = cudaError_t) */
+
+#define LGS_MAX_VIEWS 64
+#define LGS_MAX_SH_DEGREE 3
+
+/* Device status buffer: LGS_STATUS_WORDS int64 words, caller-zeroed. */
+#define LGS_STATUS_WORDS 8
+#define LGS_ST_CODE 0           /* first device-side error code (0 = none) */
+#define LGS_ST_DETAIL 1         /* detail of that error (e.g. needed capacity) */
+#define LGS_ST_NUM_INSTANCES 2  /* K, written by lgs_sort */
+#define LGS_ST_NONFINITE 3      /* Gaussians with non-finite inputs (culled), accumulated */
+#define LGS_ST_PAIRS 4          /* pixel-Gaussian pairs of the render schedule (LGS_FLAG_COUNT) */
+#define LGS_ST_QUEUE 5          /* work-queue counter of the persistent render (library-owned) */
+#define LGS_ST_QUEUE_BWD 6      /* work-queue counter of the persistent backward (library-owned) */
+#define LGS_ST_SPARE 7
+
+/* Pinhole camera. Pixel (x, y) is sampled at the integer position (x, y);
+ * u = fx * X/Z + cx, v = fy * Y/Z + cy for a camera-space point (X, Y, Z).
+ * viewmat is the row-major 4x4 world-to-camera transform with OpenCV axes
+ * (x right, y down, z forward); only its top 3x4 block is read. campos is the
+ * camera centre in world space (used for the SH view direction); bg the
+ * background colour composited with the final transmittance. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[16];
+    float campos[3];
+    float bg[3];
+} lgs_camera;
+
+/* Scene: N Gaussians, structure-of-arrays, float32, device memory.
+ * means [N,3]; scales [N,3] (already exponentiated); quats [N,4] (w,x,y,z, any
+ * non-zero norm); opacities [N] (already in (0,1)); sh [N,(d+1)^2,3] with
+ * d = sh_degree in 0..3 (16-B aligned). */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+} lgs_gaussians;
+
+#define LGS_MODE_LOCALGS 0      /* hoisting + warp culling + warp-coherent blending */
+#define LGS_MODE_PLAIN 1        /* per-pixel global-coordinate loop with per-pixel branches */
+
+#define LGS_FLAG_COUNT 1        /* render also counts its schedule's pixel-Gaussian pairs into d_status[LGS_ST_PAIRS] */
+#define LGS_FLAG_PERSISTENT 2   /* render with persistent CTAs pulling tiles from a work queue */
+
+/* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}; 8 warps per tile, each a
+ * tile_w x tile_h/8 strip), render mode and flags. batch = Gaussians staged in
+ * shared memory per round (0 = 256; 64, 128 or 256). */
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t mode;
+    int32_t batch;
+    int32_t flags;
+} lgs_config;
+
+/* Per-(view, Gaussian) preprocess outputs, M = n_views * N entries each,
+ * device memory owned by the caller.
+ *   xy      [M,4] f32 16-B aligned: (u_hi, v_hi, u_lo, v_lo), the projected mean
+ *           as an unevaluated float pair u = u_hi + u_lo (about 48 bits)
+ *   conic   [M,4] f32 16-B aligned: (a, b, c, o) with Sigma'^-1 = [[a,b],[b,c]]
+ *   rgb     [M,4] f32 16-B aligned: (r, g, b, depth)
+ *   depth   [M]   f32 camera-space z
+ *   radius  [M]   i32 ceil(3 sqrt(lambda_max)), 0 when culled
+ *   tiles   [M]   u32 number of tiles in the rect, 0 when culled
+ *   rect    [M]   u64 tile rect packed as x_lo | y_lo<<16 | x_hi<<32 | y_hi<<48 (half-open)
+ *   flags   [M]   u8  bit c (c<3): colour channel c was clamped at 0;
+ *                     bit 3/4: x/z resp. y/z clamped to 1.3 tan(fov/2) in the EWA Jacobian */
+typedef struct {
+    float* xy;
+    float* conic;
+    float* rgb;
+    float* depth;
+    int32_t* radius;
+    uint32_t* tiles;
+    uint64_t* rect;
+    uint8_t* flags;
+} lgs_pre_out;
+
+/* Gradients (device, caller-zeroed, accumulated with atomics).
+ * means [N,3], scales [N,3], quats [N,4], opacities [N], sh [N,(d+1)^2,3].
+ * The *_2d buffers are per-(view, Gaussian) scratch gradients of the render
+ * stage, M = n_views*N entries: xy2d [M,2], conic2d [M,4] (a, b, c, o), rgb2d [M,3]. */
+typedef struct {
+    float* means;
+    float* scales;
+    float* quats;
+    float* opacities;
+    float* sh;
+    float* xy2d;
+    float* conic2d;
+    float* rgb2d;
+} lgs_grads;
+
+/* Stage 1, preprocess (Sec. II-A; Fig. 2 "preprocessing"): per view and
+ * Gaussian, near-plane cull (z <= 0.2), EWA projection of the covariance with
+ * the 0.3 px low-pass term, conic, radius, tile rect, SH colour in the view
+ * direction and depth. Non-finite inputs cull the Gaussian and are counted in
+ * d_status[LGS_ST_NONFINITE]. Writes every field of *out for all M entries. */
+lgs_status lgs_preprocess(const lgs_gaussians* g, const lgs_camera* cams, int32_t n_views,
+                          const lgs_config* cfg, const lgs_pre_out* out, int64_t* d_status,
+                          void* stream);
+
+/* Workspace bytes of lgs_sort for M = n_views*N entries and an instance
+ * capacity (upper bound of K = sum of tiles). */
+size_t lgs_sort_workspace_size(int64_t m, int64_t capacity);
+
+/* Stage 2, duplicate + sort (Sec. II-A: "a parallel prefix scan duplicates the
+ * surviving primitives across intersecting tiles into 64-bit key-value pairs,
+ * which are sorted by GPU radix sort to produce ... tile ranges"):
+ * exclusive scan of tiles, emission of key = (tile_id << 32) | bits(depth) and
+ * value = v*N + i in Gaussian order (tiles row-major inside the rect), stable
+ * LSD radix sort on the 32 + ceil(log2(tiles)) significant key bits, and
+ * per-tile ranges [start, end) (0,0 for empty tiles).
+ * keys [capacity] u64, vals [capacity] u32, ranges [n_tiles_total,2] u32 (all
+ * device, caller-owned). K is written to d_status[LGS_ST_NUM_INSTANCES]; if
+ * K > capacity nothing is sorted, d_status records LGS_ERR_CAPACITY with K as
+ * detail and ranges are left empty. capacity must be < 2^32. */
+lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, int32_t n_views,
+                    const lgs_config* cfg, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                    uint32_t* ranges, void* workspace, size_t workspace_bytes, int64_t* d_status,
+                    void* stream);
+
+/* Stage 3, render (Sec. II-A render kernel; Local-GS Sec. III or the plain
+ * per-pixel kernel, cfg->mode). Per pixel, front to back over its tile's list:
+ * alpha = min(0.99, o exp(-1/2 d^T Sigma'^-1 d)) (Eq. 3DGS alpha); Gaussians with
+ * alpha < 1/255 are skipped; the pixel stops before the first Gaussian with
+ * T(1-alpha) < 1e-4; C += rgb alpha T, T *= (1-alpha).
+ * Outputs (device, concatenated per view, see header comment):
+ *   rgb [3*P] f32 = C + T bg; final_T [P] f32; n_contrib [P] u32 = list
+ *   position (1-based) of the last blended Gaussian. */
+lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* vals, const uint32_t* ranges,
+                          const lgs_camera* cams, int32_t n_views, const lgs_config* cfg,
+                          float* rgb, float* final_T, uint32_t* n_contrib, int64_t* d_status,
+                          void* stream);
+
+/* Adjoint of stages 1 and 3 (no counterpart in the paper, which covers
+ * inference only): given dL/drgb [3*P] and optionally dL/dfinal_T [P] (NULL =
+ * zero), recomputes blending back to front per tile from the stored final_T
+ * and n_contrib and accumulates gradients into *grads (caller-zeroed):
+ * first the per-(view, Gaussian) 2D gradients, then the chain rule through
+ * conic inverse, EWA, covariance, quaternion normalisation and SH. */
+lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams, int32_t n_views,
+                          const lgs_config* cfg, const lgs_pre_out* pre, const uint32_t* vals,
+                          const uint32_t* ranges, const float* final_T, const uint32_t* n_contrib,
+                          const float* dL_drgb, const float* dL_dfinal_T, const lgs_grads* grads,
+                          int64_t* d_status, void* stream);
+
+/* Copies the LGS_STATUS_WORDS device status words into h_status after
+ * synchronising `stream`. Returns LGS_ERR_CUDA if the copy fails. */
+lgs_status lgs_read_status(const int64_t* d_status, int64_t* h_status, void* stream);
+
+/* Static description of a status code. */
+const char* lgs_status_string(lgs_status s);
+
+/* Library version, (major << 16) | minor. */
+int32_t lgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGS_H */

@@ -1,0 +1,316 @@
+// render.cu -- stage 3 of the 3DGS pipeline: per-tile front-to-back alpha
+// blending (Local-GS Sec. II-A render kernel).
+//
+// render_localgs implements the three Local-GS stages (Sec. III):
+//  (1) hoisting (Sec. III-B): while a batch of the tile's Gaussians is staged
+//      into shared memory, each staging thread maps (a, b, c, ln o) and the
+//      tile-local offset Delta to the six coefficients V = [A..F] of
+//      ln(alpha) = A x'^2 + B x'y' + C y'^2 + D x' + E y' + F (Eq. hoist
+//      transform), scaled by log2(e) so that alpha = 2^(V . B_local) is one
+//      ex2. The pixel basis B_local = [x'^2, x'y', y'^2, x', y', 1] lives in
+//      registers. The tile-local origin is the tile centre rather than its
+//      corner: x' and Delta are then half as large, which divides the
+//      cancellation bound of Sec. III-B4 by four at no cost.
+//  (2) warp-level culling (Sec. III-C): the staging thread also evaluates the
+//      tight box of the Gaussian's ellipse a x~^2 + 2b x~y~ + c y~^2 = tau,
+//      tau = 2 ln(255 o), restricted to the tile column (Cases A/B/C), and turns
+//      its vertical span into an 8-bit mask of warp strips. Each warp then
+//      compacts the batch with __ballot_sync on its mask bit and walks only
+//      the set bits, so culled Gaussians cost no issue slot at all.
+//  (3) warp-coherent blending (Sec. III-D): the per-pair data path is a fixed
+//      branch-free sequence (5 FMA dot product, ex2, clamp, predicated
+//      threshold/stop, w = alpha T, 3 FMA colour, 1 FMA transmittance); the
+//      warp leaves the list when __all_sync says every lane is done.
+// The alpha >= 1/255 skip and the per-pixel stop before T(1-alpha) < 1e-4 are
+// kept as predicates (not branches), so results follow the per-pixel
+// definition exactly; the warp-uniform exit only saves work.
+//
+// render_plain is the comparison baseline: the same staging and tile lists, but
+// each thread evaluates every staged Gaussian in global pixel coordinates with
+// per-pixel branches and per-pixel early exit (Alg. 1 left column).
+#include "common.cuh"
+#include "host.h"
+
+namespace lgs {
+
+constexpr int BATCH = 256;
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LOG2_ALPHA_MIN = -7.9943534368588580f;  // log2(1/255)
+constexpr float LN255 = 5.5412635451584258f;
+
+struct RenderParams {
+    const float4* xy;
+    const float4* conic;
+    const float4* rgb;
+    const uint32_t* vals;
+    const uint2* ranges;
+    float* out_rgb;
+    float* out_T;
+    uint32_t* out_n;
+    int64_t* status;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Warp-strip mask of one Gaussian for one tile (Sec. III-C2/C3), evaluated
+// conservatively: tau is widened (relative 1e-3, absolute 0.02) and the span by
+// 1/64 px, so every pixel whose FP32 alpha clears 1/255 lies in a set strip.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_mask(float a, float b, float c, float o, float mux,
+                                              float muy, int X0, int Y0) {
+    constexpr int ROWS = TH / 8;
+    float tau = 2.f * (LN255 + __logf(o));
+    tau = fmaf(tau, 1.001f, 0.02f);
+    if (!(tau > 0.f)) return 0u;
+    const float det = fmaf(a, c, -b * b);
+    if (!(det > 0.f)) return 0xffu;
+    const float ct = c * tau, at = a * tau;
+    const float xr = sqrtf(ct / det);
+    float x0 = (float)X0 - mux, x1 = (float)(X0 + TW - 1) - mux;
+    if (x1 < -xr || x0 > xr) return 0u;
+    x0 = fmaxf(x0, -xr);
+    x1 = fminf(x1, xr);
+    const float dy = sqrtf(at / det);
+    float ymax, ymin;
+    if (-b * dy < a * x0)      ymax = (-b * x0 + sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
+    else if (-b * dy > a * x1) ymax = (-b * x1 + sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
+    else                       ymax = dy;
+    if (b * dy < a * x0)       ymin = (-b * x0 - sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
+    else if (b * dy > a * x1)  ymin = (-b * x1 - sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
+    else                       ymin = -dy;
+    const float ylo = fmaxf((float)Y0, muy + ymin - 0.015625f);
+    const float yhi = fminf((float)(Y0 + TH - 1), muy + ymax + 0.015625f);
+    if (!(ylo <= yhi)) return 0u;
+    const int ys = (int)ceilf(ylo), ye = (int)floorf(yhi);
+    if (ys > ye) return 0u;
+    const int ws = (ys - Y0) / ROWS, we = (ye - Y0) / ROWS;
+    return ((1u << (we - ws + 1)) - 1u) << ws;
+}
+
+struct TileCtx {
+    int view, X0, Y0, px, py, lx, ly;
+    bool inside;
+    uint32_t start, count;
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ TileCtx tile_ctx(const Views& vs, const RenderParams& p, uint32_t tile) {
+    TileCtx t;
+    t.view = view_of_tile(vs, tile);
+    const ViewRec& c = vs.v[t.view];
+    const uint32_t lt = tile - c.tile_off;
+    const int tx = (int)(lt % (uint32_t)c.gx), ty = (int)(lt / (uint32_t)c.gx);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    t.lx = lane % TW;
+    t.ly = warp * (TH / 8) + lane / TW;
+    t.X0 = tx * TW;
+    t.Y0 = ty * TH;
+    t.px = t.X0 + t.lx;
+    t.py = t.Y0 + t.ly;
+    t.inside = t.px < c.W && t.py < c.H;
+    const uint2 r = p.ranges[tile];
+    t.start = r.x;
+    t.count = r.y - r.x;
+    return t;
+}
+
+__device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams& p, const TileCtx& t,
+                                            float C0, float C1, float C2, float T, uint32_t last) {
+    if (!t.inside) return;
+    const ViewRec& c = vs.v[t.view];
+    const int64_t plane = (int64_t)c.W * c.H;
+    const int64_t pix = (int64_t)t.py * c.W + t.px;
+    float* o = p.out_rgb + 3 * (int64_t)c.pix_off;
+    o[pix] = fmaf(T, c.bg[0], C0);
+    o[plane + pix] = fmaf(T, c.bg[1], C1);
+    o[2 * plane + pix] = fmaf(T, c.bg[2], C2);
+    p.out_T[c.pix_off + pix] = T;
+    p.out_n[c.pix_off + pix] = last;
+}
+
+// ------------------------------------------------------------------ Local-GS
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
+    __shared__ float4 sV[BATCH];   // (A, B, C, F), log2 domain
+    __shared__ float2 sDE[BATCH];  // (D, E)
+    __shared__ float4 sC[BATCH];   // (r, g, b, -)
+    __shared__ uint8_t sM[BATCH];  // warp-strip mask
+
+    const TileCtx t = tile_ctx<TW, TH>(vs, p, blockIdx.x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float Ox = (float)t.X0 + 0.5f * (TW - 1), Oy = (float)t.Y0 + 0.5f * (TH - 1);
+    const float xl = (float)t.lx - 0.5f * (TW - 1), yl = (float)t.ly - 0.5f * (TH - 1);
+    const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0;
+    bool done = !t.inside;
+    bool warp_done = __all_sync(0xffffffffu, done);
+    uint32_t pairs = 0;
+
+    for (uint32_t b0 = 0; b0 < t.count; b0 += BATCH) {
+        if (__syncthreads_and(warp_done)) break;
+        const uint32_t j = b0 + threadIdx.x;
+        if (j < t.count) {
+            const uint32_t id = p.vals[t.start + j];
+            const float4 xy = p.xy[id];
+            const float4 co = p.conic[id];
+            const float4 col = p.rgb[id];
+            const float dx = __fadd_rn(xy.x - Ox, xy.z);
+            const float dy = __fadd_rn(xy.y - Oy, xy.w);
+            const float Dn = fmaf(co.x, dx, co.y * dy);
+            const float En = fmaf(co.y, dx, co.z * dy);
+            const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
+            sV[threadIdx.x] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
+                                          fmaf(Fn, LOG2E, __log2f(co.w)));
+            sDE[threadIdx.x] = make_float2(Dn * LOG2E, En * LOG2E);
+            sC[threadIdx.x] = col;
+            sM[threadIdx.x] = (uint8_t)warp_mask<TW, TH>(co.x, co.y, co.z, co.w, xy.x + xy.z,
+                                                         xy.y + xy.w, t.X0, t.Y0);
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)BATCH, t.count - b0);
+        if (!warp_done) {
+            for (int c0 = 0; c0 < nb; c0 += 32) {
+                const int jj = c0 + lane;
+                uint32_t bits = __ballot_sync(0xffffffffu, jj < nb && ((sM[jj] >> warp) & 1u));
+                while (bits) {
+                    const int k = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (COUNT) {
+                        if (__all_sync(0xffffffffu, done)) { bits = 0; break; }
+                        ++pairs;
+                    }
+                    const int g = c0 + k;
+                    const float4 V = sV[g];
+                    const float2 DE = sDE[g];
+                    const float4 col = sC[g];
+                    const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
+                                     fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
+                    const float al = fminf(0.99f, ex2_approx(pw));
+                    const bool valid = !done && pw >= LOG2_ALPHA_MIN;
+                    const float tT = fmaf(-al, T, T);
+                    const bool stop = valid && tT < 1e-4f;
+                    const bool blend = valid && !stop;
+                    done = done || stop;
+                    const float w = blend ? al * T : 0.f;
+                    C0 = fmaf(col.x, w, C0);
+                    C1 = fmaf(col.y, w, C1);
+                    C2 = fmaf(col.z, w, C2);
+                    T = blend ? tT : T;
+                    last = blend ? (b0 + (uint32_t)g + 1u) : last;
+                }
+                if (__all_sync(0xffffffffu, done)) { warp_done = true; break; }
+            }
+        }
+        __syncthreads();
+    }
+    write_pixel(vs, p, t, C0, C1, C2, T, last);
+    if (COUNT && lane == 0 && pairs)
+        atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_PAIRS),
+                  (unsigned long long)pairs * 32ull);
+}
+
+// ------------------------------------------------------------------ plain
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
+    __shared__ float4 sXY[BATCH];
+    __shared__ float4 sCO[BATCH];
+    __shared__ float4 sC[BATCH];
+
+    const TileCtx t = tile_ctx<TW, TH>(vs, p, blockIdx.x);
+    const float pxf = (float)t.px, pyf = (float)t.py;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0;
+    bool done = !t.inside;
+    uint32_t pairs = 0;
+
+    for (uint32_t b0 = 0; b0 < t.count; b0 += BATCH) {
+        if (__syncthreads_count(done) == (int)blockDim.x) break;
+        const uint32_t j = b0 + threadIdx.x;
+        if (j < t.count) {
+            const uint32_t id = p.vals[t.start + j];
+            sXY[threadIdx.x] = p.xy[id];
+            sCO[threadIdx.x] = p.conic[id];
+            sC[threadIdx.x] = p.rgb[id];
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)BATCH, t.count - b0);
+        for (int g = 0; !done && g < nb; ++g) {
+            if (COUNT && (threadIdx.x & 31) == (__ffs(__activemask()) - 1)) ++pairs;
+            const float4 xy = sXY[g];
+            const float dx = __fadd_rn(xy.x - pxf, xy.z);
+            const float dy = __fadd_rn(xy.y - pyf, xy.w);
+            const float4 co = sCO[g];
+            const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+            if (power > 0.f) continue;
+            const float alpha = fminf(0.99f, co.w * __expf(power));
+            if (alpha < 1.f / 255.f) continue;
+            const float test_T = T * (1.f - alpha);
+            if (test_T < 1e-4f) { done = true; continue; }
+            const float4 col = sC[g];
+            C0 += col.x * alpha * T;
+            C1 += col.y * alpha * T;
+            C2 += col.z * alpha * T;
+            T = test_T;
+            last = b0 + (uint32_t)g + 1u;
+        }
+        __syncthreads();
+    }
+    write_pixel(vs, p, t, C0, C1, C2, T, last);
+    if (COUNT && pairs)
+        atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_PAIRS),
+                  (unsigned long long)pairs * 32ull);
+}
+
+template <int TW, int TH>
+lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, bool count,
+                         cudaStream_t s) {
+    const dim3 grid(vs.n_tiles), block(256);
+    if (mode == LGS_MODE_PLAIN) {
+        if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
+        else       render_plain<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
+    } else {
+        if (count) render_localgs<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
+        else       render_localgs<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lgs
+
+using namespace lgs;
+
+extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* vals,
+                                     const uint32_t* ranges, const lgs_camera* cams,
+                                     int32_t n_views, const lgs_config* cfg, float* rgb,
+                                     float* final_T, uint32_t* n_contrib, int64_t* d_status,
+                                     void* stream) {
+    if (!vals || !ranges || !rgb || !final_T || !n_contrib || !d_status) return LGS_ERR_ARG;
+    Views vs;
+    lgs_status st = make_views(cams, n_views, cfg, &vs);
+    if (st != LGS_OK) return st;
+    st = check_pre(pre);
+    if (st != LGS_OK) return st;
+    if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
+    if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
+    RenderParams p;
+    p.xy = reinterpret_cast<const float4*>(pre->xy);
+    p.conic = reinterpret_cast<const float4*>(pre->conic);
+    p.rgb = reinterpret_cast<const float4*>(pre->rgb);
+    p.vals = vals;
+    p.ranges = reinterpret_cast<const uint2*>(ranges);
+    p.out_rgb = rgb;
+    p.out_T = final_T;
+    p.out_n = n_contrib;
+    p.status = d_status;
+    const bool count = (cfg->flags & LGS_FLAG_COUNT) != 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, count, s);
+    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, count, s);
+    return launch_render<32, 8>(p, vs, cfg->mode, count, s);
+}

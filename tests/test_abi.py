@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/lgs.h
+declares; host-side argument checks return errors before touching a GPU."""
+import ctypes
+import os
+import re
+
+from paper_2606_16566_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lgs_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.load()
+    declared = _declared()
+    assert {"lgs_preprocess", "lgs_sort", "lgs_render_fwd", "lgs_render_bwd"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(L.SIGNATURES) >= declared
+
+
+def test_status_strings_and_version():
+    lib = L.load()
+    assert lib.lgs_version() >= 1
+    for code in range(8):
+        assert lib.lgs_status_string(code)
+    assert b"capacity" in lib.lgs_status_string(L.LGS_ERR_CAPACITY)
+
+
+def test_host_side_argument_checks_need_no_gpu():
+    lib = L.load()
+    cam = (L.lgs_camera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 64, 48, 50.0, 50.0
+    cfg = L.lgs_config(16, 16, 0, 0, 0)
+    pre = L.lgs_pre_out()
+    g = L.lgs_gaussians()
+    # NULL output structure pointers -> LGS_ERR_ARG before any launch
+    assert lib.lgs_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(cfg), None, None, None) == L.LGS_ERR_ARG
+    # unsupported tile shape
+    bad = L.lgs_config(12, 12, 0, 0, 0)
+    fake = ctypes.c_void_p(16)
+    pre2 = L.lgs_pre_out(*([16] * 8))
+    assert lib.lgs_render_fwd(ctypes.byref(pre2), fake, fake, cam, 1, ctypes.byref(bad), fake, fake,
+                              fake, fake, None) == L.LGS_ERR_UNSUPPORTED
+    # too many views
+    assert lib.lgs_render_fwd(ctypes.byref(pre2), fake, fake, cam, 65, ctypes.byref(cfg), fake,
+                              fake, fake, fake, None) == L.LGS_ERR_UNSUPPORTED
+    # misaligned float4 array
+    pre3 = L.lgs_pre_out(*([16] * 8))
+    pre3.xy = 20
+    assert lib.lgs_render_fwd(ctypes.byref(pre3), fake, fake, cam, 1, ctypes.byref(cfg), fake,
+                              fake, fake, fake, None) == L.LGS_ERR_ALIGN
+    # workspace too small for the sort
+    assert lib.lgs_sort(ctypes.byref(pre2), 10, cam, 1, ctypes.byref(cfg), 100, fake, fake, fake,
+                        fake, 1, fake, None) == L.LGS_ERR_ARG
+    assert lib.lgs_sort_workspace_size(10, 100) > 0
+    assert pre.xy is None

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer outputs (radius, tiles, rect, depth key bits, per-tile Gaussian
+lists, n_contrib) are bit-exact outside guard items; images meet
+max |err| <= 2e-3 with at most 1e-4 of the pixels above 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_16566_gb300 import lgs, scenes
+from paper_2606_16566_gb300 import _lib as L
+
+from parity import (assert_image_parity, compare_preprocess, full_view_parity, gpu_pre_numpy,
+                    guard_gaussians, to_numpy_view)
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(16, 16), (8, 32), (32, 8)]
+
+
+def _render(scene, cams, tile=(16, 16), mode="localgs", **kw):
+    g = lgs.to_device(scene)
+    return lgs.render(g, cams, tile=tile, mode=mode, **kw)
+
+
+# --------------------------------------------------------------------------- preprocess
+@pytest.mark.parametrize("seed,deg", [(1, 0), (2, 1), (3, 2), (4, 3)])
+def test_preprocess_matches_oracle(seed, deg):
+    sc, cams = scenes.random_small(3000, seed=seed, width=200, height=150, sh_degree=deg)
+    res = _render(sc, cams)
+    torch.cuda.synchronize()
+    g = gpu_pre_numpy(res["pre"], 3000)
+    o = oracle.preprocess(sc, cams[0])
+    rep = compare_preprocess(g, o, guard_gaussians(o))
+    print(rep)
+    assert rep["radius_mismatch"] == 0 and rep["tiles_mismatch"] == 0, rep
+    assert rep["rect_mismatch"] == 0 and rep["depth_mismatch"] == 0, rep
+    assert rep["guard"] <= max(1, 1e-4 * 3000), rep
+    assert rep["uv_max_err"] < 1e-6, rep
+    assert rep["rgb_max_err"] < 1e-5, rep
+    assert rep["conic_max_rel"] < 1e-4, rep
+
+
+def test_preprocess_culls_and_counts_nonfinite():
+    sc, cams = scenes.random_small(64, seed=5)
+    sc["means"][3] = [np.nan, 0, 0]
+    sc["scales"][7, 1] = np.inf
+    sc["means"][9] = [0.0, 0.0, -10.0]        # behind the camera
+    res = _render(sc, cams)
+    st = lgs.read_status(res["status"])
+    assert st[L.ST_NONFINITE] == 2
+    tiles = res["pre"].tiles.cpu().numpy()
+    assert tiles[3] == 0 and tiles[7] == 0 and tiles[9] == 0
+
+
+# --------------------------------------------------------------------------- sort
+def _host_sort_of_gpu_keys(res, cams, n, tile):
+    """Stable sort, on the host, of the keys re-emitted from the GPU's own
+    preprocess outputs: the GPU sort must match it bit for bit (no guard)."""
+    tw, th = tile
+    pre = gpu_pre_numpy(res["pre"], n * len(cams))
+    keys, vals = [], []
+    toff = 0
+    for v, c in enumerate(cams):
+        gx = (c["width"] + tw - 1) // tw
+        for i in range(n):
+            m = v * n + i
+            if pre["tiles"][m] == 0:
+                continue
+            x0, y0, x1, y1 = pre["rect"][m]
+            for ty in range(y0, y1):
+                for tx in range(x0, x1):
+                    keys.append(((toff + ty * gx + tx) << 32) | int(pre["depth_bits"][m]))
+                    vals.append(m)
+        toff += gx * ((c["height"] + th - 1) // th)
+    keys = np.array(keys, dtype=np.uint64)
+    vals = np.array(vals, dtype=np.uint32)
+    order = np.argsort(keys, kind="stable")
+    return keys[order], vals[order], toff
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_sort_bitexact_against_host_stable_sort(tile):
+    sc, cams = scenes.random_small(800, seed=9, width=170, height=130)
+    cams = cams + [scenes.look_at((2.0, 1.0, -3.0), (0, 0, 0), 97, 61, 70.0)]
+    res = _render(sc, cams, tile=tile)
+    k_ref, v_ref, nt = _host_sort_of_gpu_keys(res, cams, 800, tile)
+    assert res["K"] == len(k_ref)
+    np.testing.assert_array_equal(res["keys"].cpu().numpy().view(np.uint64), k_ref)
+    np.testing.assert_array_equal(res["vals"].cpu().numpy().view(np.uint32), v_ref)
+    ranges = res["ranges"].cpu().numpy().view(np.uint32)
+    tid = (k_ref >> np.uint64(32)).astype(np.int64)
+    for t in range(nt):
+        idx = np.nonzero(tid == t)[0]
+        if len(idx):
+            assert tuple(ranges[t]) == (idx[0], idx[-1] + 1)
+        else:
+            assert tuple(ranges[t]) == (0, 0)
+
+
+def test_sort_many_instances_multi_pass():
+    """Enough instances for many 4096-key blocks and >5 radix passes."""
+    sc, cams = scenes.random_small(20000, seed=10, width=640, height=480, log_scale_mean=-2.5)
+    res = _render(sc, cams)
+    k = res["keys"].cpu().numpy().view(np.uint64)
+    assert res["K"] > 50000
+    assert np.all(k[1:] >= k[:-1])
+    k_ref, v_ref, _ = _host_sort_of_gpu_keys(res, cams, 20000, (16, 16))
+    np.testing.assert_array_equal(k, k_ref)
+    np.testing.assert_array_equal(res["vals"].cpu().numpy().view(np.uint32), v_ref)
+
+
+def test_capacity_overflow_reports_needed_count():
+    sc, cams = scenes.random_small(500, seed=11)
+    g = lgs.to_device(sc)
+    cfg = lgs.config()
+    status = lgs.new_status()
+    pre = lgs.preprocess(g, cams, cfg, status=status)
+    lgs.sort(pre, 500, cams, cfg, 10, status=status)
+    st = lgs.read_status(status)
+    assert st[L.ST_CODE] == L.LGS_ERR_CAPACITY
+    assert st[L.ST_DETAIL] == st[L.ST_NUM_INSTANCES] > 10
+    res = _render(sc, cams)                       # the retry path sizes itself
+    assert res["K"] == st[L.ST_DETAIL]
+
+
+# --------------------------------------------------------------------------- render
+@pytest.mark.parametrize("mode", ["localgs", "plain"])
+@pytest.mark.parametrize("tile", TILES)
+def test_render_matches_oracle_small(mode, tile):
+    sc, cams = scenes.random_small(2500, seed=21, width=181, height=133)
+    res = _render(sc, cams, tile=tile, mode=mode)
+    view = to_numpy_view(res, 0, cams, 2500, tile)
+    rep, _ = full_view_parity(sc, cams[0], view, tile)
+    print(mode, tile, rep)
+    assert not rep["unexplained_tiles"], rep
+    assert rep["n_contrib_mismatch"] == 0, rep
+    assert_image_parity(rep, f"{mode} {tile}")
+
+
+def test_render_tiny_config_matches_oracle():
+    sc, cams = scenes.tiny()
+    res = _render(sc, cams)
+    view = to_numpy_view(res, 0, cams, sc["means"].shape[0], (16, 16))
+    rep, _ = full_view_parity(sc, cams[0], view, (16, 16))
+    print(rep)
+    assert not rep["unexplained_tiles"] and rep["n_contrib_mismatch"] == 0, rep
+    assert_image_parity(rep, "tiny")
+
+
+def test_multiview_batch_equals_single_views():
+    sc, cams = scenes.outdoor(n=20000, width=160, height=104, n_views=3)
+    cams = cams + [scenes.look_at((0.5, 3.0, 5.0), (0, 0, 0), 121, 77, 50.0)]
+    res = _render(sc, cams)
+    for v in range(len(cams)):
+        one = _render(sc, [cams[v]])
+        torch.testing.assert_close(res["rgb"][v], one["rgb"][0], rtol=0, atol=0)
+        torch.testing.assert_close(res["n_contrib"][v], one["n_contrib"][0], rtol=0, atol=0)
+
+
+def test_localgs_equals_plain_integer_outputs():
+    sc, cams = scenes.random_small(4000, seed=23, width=256, height=200, log_scale_mean=-2.8)
+    a = _render(sc, cams, mode="localgs")
+    b = _render(sc, cams, mode="plain")
+    na, nb = a["n_contrib"][0].cpu().numpy(), b["n_contrib"][0].cpu().numpy()
+    assert np.mean(na != nb) <= 1e-3
+    err = (a["rgb"][0] - b["rgb"][0]).abs().max().item()
+    assert err <= 2e-3
+
+
+def test_empty_and_degenerate_inputs():
+    sc, cams = scenes.random_small(10, seed=3)
+    empty = {k: v[:0] for k, v in sc.items()}
+    res = _render(empty, cams)
+    assert res["K"] == 0
+    bg = torch.tensor(cams[0]["bg"]).cuda()
+    assert torch.allclose(res["rgb"][0], bg[:, None, None].expand_as(res["rgb"][0]))
+    assert torch.all(res["final_T"][0] == 1)
+    # everything behind the camera
+    sc["means"][:, 2] = -10.0
+    res = _render(sc, cams)
+    assert res["K"] == 0
+    # 1x1 image and an image narrower than a tile
+    for W, H in [(1, 1), (5, 37)]:
+        sc2, cams2 = scenes.random_small(300, seed=4, width=W, height=H)
+        r = _render(sc2, cams2)
+        view = to_numpy_view(r, 0, cams2, 300, (16, 16))
+        rep, _ = full_view_parity(sc2, cams2[0], view, (16, 16))
+        assert rep["n_contrib_mismatch"] == 0 and rep["max_abs"] <= 2e-3, rep
+
+
+def test_schedule_pair_count_vs_oracle():
+    """LGS_FLAG_COUNT counts the pixel-Gaussian pairs of the Local-GS schedule
+    (mask bit set, up to the warp's exit). The GPU mask is a conservative
+    superset of the exact FP64 mask, so the count is >= the oracle's and
+    within 2% of it."""
+    sc, cams = scenes.random_small(3000, seed=31, width=200, height=160)
+    res = _render(sc, cams, flags=L.FLAG_COUNT)
+    gpu_pairs = lgs.read_status(res["status"])[L.ST_PAIRS]
+    o = oracle.render(sc, cams[0])
+    ref = oracle.localgs_pairs(o, cams[0])
+    assert ref > 0
+    assert ref <= gpu_pairs <= 1.02 * ref, (gpu_pairs, ref)
+
+
+@pytest.mark.parametrize("v", [0, 5])
+def test_outdoor_full_size_views(v):
+    """Full outdoor workload (500k Gaussians, 8 views of 1264x832 in one batch,
+    the benchmark's launch configuration); two views checked in full."""
+    sc, cams = scenes.outdoor()
+    res = _render(sc, cams)
+    view = to_numpy_view(res, v, cams, sc["means"].shape[0], (16, 16))
+    rep, _ = full_view_parity(sc, cams[v], view, (16, 16))
+    print(rep)
+    assert not rep["unexplained_tiles"], rep["unexplained_tiles"][:10]
+    assert rep["n_contrib_mismatch"] <= 1e-4 * rep["n_pix"], rep
+    assert_image_parity(rep, f"outdoor view {v}")
