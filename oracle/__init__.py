@@ -54,7 +54,7 @@ def lib():
         L.orc_quat_to_rot.argtypes = [_dp, _dp]
         L.orc_cov3d.argtypes = [_dp, _dp, _dp]
         L.orc_ewa.argtypes = [_dp, _dp, _dp, _dp]
-        L.orc_preprocess.argtypes = [ctypes.c_int64, ctypes.c_int, _fp, _fp, _fp, _fp, _fp,
+        L.orc_preprocess.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
                                      _dp, ctypes.c_int, ctypes.c_int, _dp,
                                      _dp, _dp, _u32p, _dp, _i32p, _i32p, _i64p, _dp, _u8p, _u8p]
         L.orc_sort.restype = ctypes.c_int64
@@ -62,14 +62,14 @@ def lib():
                                ctypes.c_uint32, _i32p, _i64p, _u32p, ctypes.c_int64,
                                _u64p, _u32p, _u32p]
         L.orc_blend.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
-                                _u32p, _u32p, ctypes.c_int64, _dp, _dp, _fp, _dp, _dp,
+                                _u32p, _u32p, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
                                 _dp, _dp, _u32p, _u8p, _u32p, _u32p]
         L.orc_hoist.argtypes = [ctypes.c_double] * 6 + [_dp]
         L.orc_warp_mask.restype = ctypes.c_uint32
         L.orc_warp_mask.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int] * 5
         L.orc_localgs_pairs.restype = ctypes.c_int64
         L.orc_localgs_pairs.argtypes = [ctypes.c_int] * 5 + [_u32p, _u32p, ctypes.c_int64,
-                                                             _dp, _dp, _fp, _u32p]
+                                                             _dp, _dp, _dp, _u32p]
         if hasattr(L, "orc_backward"):
             _bind_backward(L)
         _LIB = L
@@ -77,8 +77,8 @@ def lib():
 
 
 def _bind_backward(L):
-    L.orc_backward.argtypes = [ctypes.c_int64, ctypes.c_int, _fp, _fp, _fp, _fp, _fp, _dp,
-                               ctypes.c_int, ctypes.c_int, _u32p, _u32p, _dp, _dp,
+    L.orc_backward.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                               ctypes.c_int, ctypes.c_int, _dp, _dp,
                                _dp, _dp, _dp, _dp, _dp, _dp]
 
 
@@ -100,8 +100,12 @@ def cam_array(cam) -> np.ndarray:
         np.asarray(cam["bg"], np.float64)]).astype(np.float64)
 
 
-def _f32(x):
-    return np.ascontiguousarray(x, dtype=np.float32)
+def _in(x, exact=False):
+    """Scene array as float64: the float32 values promoted exactly, or (exact=True,
+    for finite differences) the given doubles unchanged."""
+    if exact:
+        return np.ascontiguousarray(x, dtype=np.float64)
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32), dtype=np.float64)
 
 
 def sh_degree_of(scene) -> int:
@@ -109,11 +113,11 @@ def sh_degree_of(scene) -> int:
     return int(round(k ** 0.5)) - 1
 
 
-def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
+def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False):
     L = lib()
     n = scene["means"].shape[0]
     deg = sh_degree_of(scene)
-    m, s, q, o, sh = (_f32(scene[k]) for k in ("means", "scales", "quats", "opacities", "sh"))
+    m, s, q, o, sh = (_in(scene[k], exact) for k in ("means", "scales", "quats", "opacities", "sh"))
     c = cam_array(cam)
     g = np.ascontiguousarray(guard, dtype=np.float64)
     out = {
@@ -123,7 +127,7 @@ def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
         "rgb": np.zeros((n, 3)), "clamped": np.zeros((n, 3), np.uint8),
         "gflags": np.zeros(n, np.uint8),
     }
-    L.orc_preprocess(n, deg, _p(m, _fp), _p(s, _fp), _p(q, _fp), _p(o, _fp), _p(sh, _fp),
+    L.orc_preprocess(n, deg, _p(m, _dp), _p(s, _dp), _p(q, _dp), _p(o, _dp), _p(sh, _dp),
                      _p(c, _dp), tile_w, tile_h, _p(g, _dp),
                      _p(out["uv"], _dp), _p(out["depth"], _dp), _p(out["depth_bits"], _u32p),
                      _p(out["conic"], _dp), _p(out["radius"], _i32p), _p(out["rect"], _i32p),
@@ -162,16 +166,16 @@ def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
     v = np.ascontiguousarray(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
     g = np.ascontiguousarray(guard, dtype=np.float64)
     L.orc_blend(W, H, tile_w, tile_h, _p(bg, _dp), _p(v, _u32p), _p(ranges, _u32p), 0,
-                _p(pre["uv"], _dp), _p(pre["conic"], _dp), _p(pre["opacity"], _fp),
+                _p(pre["uv"], _dp), _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
                 _p(pre["rgb"], _dp), _p(g, _dp), _p(out_rgb, _dp), _p(final_T, _dp),
                 _p(n_contrib, _u32p), _p(pguard, _u8p), _p(stop_pos, _u32p), _p(n_useful, _u32p))
     return {"rgb": out_rgb, "final_T": final_T, "n_contrib": n_contrib, "pguard": pguard,
             "stop_pos": stop_pos, "n_useful": n_useful}
 
 
-def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
+def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False):
     """Full forward pass for one view: preprocess, sort, blend."""
-    pre = preprocess(scene, cam, tile_w, tile_h, guard)
+    pre = preprocess(scene, cam, tile_w, tile_h, guard, exact)
     keys, vals, ranges = sort(pre, cam, tile_w, tile_h)
     img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard)
     img.update({"pre": pre, "keys": keys, "vals": vals, "ranges": ranges})
@@ -195,8 +199,28 @@ def localgs_pairs(res, cam, tile_w=16, tile_h=16, n_warps=8):
     v = np.ascontiguousarray(res["vals"], np.uint32) if len(res["vals"]) else np.zeros(1, np.uint32)
     return int(lib().orc_localgs_pairs(W, H, tile_w, tile_h, n_warps, _p(v, _u32p),
                                        _p(res["ranges"], _u32p), 0, _p(pre["uv"], _dp),
-                                       _p(pre["conic"], _dp), _p(pre["opacity"], _fp),
+                                       _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
                                        _p(np.ascontiguousarray(res["stop_pos"]), _u32p)))
+
+
+def backward(scene, cam, dL_drgb, dL_dT=None, tile_w=16, tile_h=16, exact=False):
+    """Hand adjoint of render() for L = <dL_drgb, rgb> + <dL_dT, final_T>.
+    Returns gradients w.r.t. means, scales, quats, opacities, sh and the 2D
+    per-Gaussian gradients g2d [N, 9] = dL/d(u, v, a, b, c, o, r, g, b)."""
+    L = lib()
+    n = scene["means"].shape[0]
+    deg = sh_degree_of(scene)
+    m, s, q, o, sh = (_in(scene[k], exact) for k in ("means", "scales", "quats", "opacities", "sh"))
+    c = cam_array(cam)
+    g = np.ascontiguousarray(dL_drgb, np.float64)
+    gT = None if dL_dT is None else np.ascontiguousarray(dL_dT, np.float64)
+    out = {"means": np.zeros((n, 3)), "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
+           "opacities": np.zeros(n), "sh": np.zeros(sh.shape), "g2d": np.zeros((n, 9))}
+    L.orc_backward(n, deg, _p(m, _dp), _p(s, _dp), _p(q, _dp), _p(o, _dp), _p(sh, _dp), _p(c, _dp),
+                   tile_w, tile_h, _p(g, _dp), None if gT is None else _p(gT, _dp),
+                   _p(out["means"], _dp), _p(out["scales"], _dp), _p(out["quats"], _dp),
+                   _p(out["opacities"], _dp), _p(out["sh"], _dp), _p(out["g2d"], _dp))
+    return out
 
 
 def sh_basis(l, m, d):
@@ -228,7 +252,7 @@ def ewa(cam, t, Sig):
     return out
 
 
-__all__ = ["render", "preprocess", "sort", "blend", "hoist", "warp_mask", "localgs_pairs",
+__all__ = ["render", "backward", "preprocess", "sort", "blend", "hoist", "warp_mask", "localgs_pairs",
            "sh_basis", "quat_to_rot", "cov3d", "ewa", "num_threads", "cam_array",
            "DEFAULT_GUARD"]
 os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")

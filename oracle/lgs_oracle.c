@@ -19,8 +19,9 @@
  * SH colour; those steps follow the standard definitions (readings listed
  * beside each function).
  *
- * Floating point: all arithmetic in double. Inputs are float32 arrays and are
- * promoted to double on load.
+ * Floating point: all arithmetic and all inputs in double. The Python wrapper
+ * passes the float32 scene values promoted exactly to double; finite-difference
+ * checks pass perturbed doubles.
  *
  * Parity status of each function is pinned by the CPU test-suite:
  *   orc_preprocess   pinned (closed form single Gaussian, EWA Jacobian by
@@ -186,8 +187,8 @@ static double int_dist_in(double q, int lo, int hi) {
  *   rgb[3i..]     max(0, SH colour + 0.5); clamped[3i..] = pre-clamp value < 0
  *   gflags[i]     guard bits (decision within its guard band)
  */
-void orc_preprocess(int64_t n, int sh_degree, const float* means, const float* scales,
-                    const float* quats, const float* opac, const float* sh,
+void orc_preprocess(int64_t n, int sh_degree, const double* means, const double* scales,
+                    const double* quats, const double* opac, const double* sh,
                     const double* cam, int tile_w, int tile_h, const double* guard,
                     double* uv, double* depth, uint32_t* depth_bits, double* conic,
                     int32_t* radius, int32_t* rect, int64_t* tiles, double* rgb,
@@ -333,7 +334,7 @@ int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_of
  * arrays directly. */
 void orc_blend(int W, int H, int tile_w, int tile_h, const double* bg,
                const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
-               const double* uv, const double* conic, const float* opac, const double* rgb,
+               const double* uv, const double* conic, const double* opac, const double* rgb,
                const double* guard, double* out_rgb, double* final_T, uint32_t* n_contrib,
                uint8_t* pguard, uint32_t* stop_pos, uint32_t* n_useful) {
     int gx = (W + tile_w - 1) / tile_w;
@@ -435,7 +436,7 @@ uint32_t orc_warp_mask(double a, double b, double c, double o, double mux, doubl
  * triggered the stop, or 0 when the pixel never stopped. */
 int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
                           const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
-                          const double* uv, const double* conic, const float* opac,
+                          const double* uv, const double* conic, const double* opac,
                           const uint32_t* stop_pos) {
     int gx = (W + tile_w - 1) / tile_w, gy = (H + tile_h - 1) / tile_h;
     int rows = tile_h / n_warps;
@@ -469,4 +470,277 @@ int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
             }
         }
     return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Hand-derived adjoint (reverse mode) of the forward map above, for a loss
+ * L = sum_pix <g_pix, rgb_pix> + sum_pix gT_pix * final_T_pix. The paper covers
+ * inference only; this is the plain chain rule through each forward step, with
+ * the piecewise-constant decisions (rects, 1/255 skips, stops, clamps) held
+ * fixed, and the true derivative of every clamp (zero slope where clamped).
+ *
+ * Blend (per pixel, blended Gaussians k in order, T_k before k):
+ *   dL/drgb_k = alpha_k T_k g
+ *   dL/dalpha_k = T_k <rgb_k, g> - (<S_k, g> + T_f <bg, g> + T_f gT)/(1 - alpha_k),
+ *                 S_k = sum_{j>k} rgb_j alpha_j T_j
+ *   alpha = o e^p (unclamped): dalpha/do = e^p, dalpha/dp = alpha
+ *   p = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = (u - px, v - py)
+ * Conic: (a, b, c) = (S11, -S01, S00)/(S00 S11 - S01^2) differentiated in
+ * (S00, S01, S11); Sigma' = T Sigma T^T + 0.3 I with T = J W:
+ *   dL/dSigma = T^T G T, dL/dT = 2 G T Sigma, G = [[g00, g01/2], [g01/2, g11]].
+ * J(t) with r = clamp(t_x/t_z): J00 = fx/tz, J02 = -fx r/tz (dr = 0 when
+ * clamped); mean u = fx tx/tz + cx; t = W mu + t_c.
+ * Sigma = M M^T, M = R(q^) diag(s): dL/dM = 2 dL/dSigma M; q^ = q/|q|.
+ * SH: rgb = max(0, sum_k Y_k(dir) sh_k + 0.5); dir = (mu - campos)/|..|;
+ * the basis gradient is taken in spherical coordinates
+ *   sin(th) dP_l^m/dth = l cos(th) P_l^m - (l+m) P_{l-1}^m.
+ * g2d (optional, n x 9): dL/d(u, v, a, b, c, o, r, g, b). */
+static void sh_grad(int deg, const double dir[3], double* Y, double (*dY)[3]) {
+    double ct = dir[2], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double phi = atan2(dir[1], dir[0]);
+    double eth[3] = { ct * cos(phi), ct * sin(phi), -st };
+    double eph[3] = { -sin(phi), cos(phi), 0.0 };
+    for (int l = 0; l <= deg; ++l)
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            int idx = l * l + l + m;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * factorial(l - am) / factorial(l + am));
+            double P = assoc_legendre(l, am, ct);
+            double Pm1 = (l - 1 >= am) ? assoc_legendre(l - 1, am, ct) : 0.0;
+            double dPdth = (st > 0.0) ? (l * ct * P - (l + am) * Pm1) / st : 0.0;
+            double trig, dtrig;
+            if (m > 0)      { trig = sqrt(2.0) * cos(m * phi); dtrig = -sqrt(2.0) * m * sin(m * phi); }
+            else if (m < 0) { trig = sqrt(2.0) * sin(am * phi); dtrig = sqrt(2.0) * am * cos(am * phi); }
+            else            { trig = 1.0; dtrig = 0.0; }
+            Y[idx] = K * P * trig;
+            double dth = K * dPdth * trig;
+            double dph = (st > 0.0) ? K * P * dtrig / st : 0.0;
+            for (int c = 0; c < 3; ++c) dY[idx][c] = dth * eth[c] + dph * eph[c];
+        }
+}
+
+void orc_backward(int64_t n, int sh_degree, const double* means, const double* scales,
+                  const double* quats, const double* opac, const double* sh, const double* cam,
+                  int tile_w, int tile_h, const double* dL_drgb, const double* dL_dT,
+                  double* g_means, double* g_scales, double* g_quats, double* g_opac,
+                  double* g_sh, double* g2d) {
+    int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
+    int gx = (W + tile_w - 1) / tile_w;
+    int Ksh = (sh_degree + 1) * (sh_degree + 1);
+    double guard0[G_SIZE] = { 0 };
+    double* uv = (double*)calloc((size_t)n * 2 + 1, sizeof(double));
+    double* depth = (double*)calloc((size_t)n + 1, sizeof(double));
+    uint32_t* dbits = (uint32_t*)calloc((size_t)n + 1, sizeof(uint32_t));
+    double* conic = (double*)calloc((size_t)n * 3 + 1, sizeof(double));
+    int32_t* radius = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t* rect = (int32_t*)calloc((size_t)n * 4 + 1, sizeof(int32_t));
+    int64_t* tiles = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    double* rgb = (double*)calloc((size_t)n * 3 + 1, sizeof(double));
+    uint8_t* clamped = (uint8_t*)calloc((size_t)n * 3 + 1, 1);
+    uint8_t* gfl = (uint8_t*)calloc((size_t)n + 1, 1);
+    orc_preprocess(n, sh_degree, means, scales, quats, opac, sh, cam, tile_w, tile_h, guard0, uv,
+                   depth, dbits, conic, radius, rect, tiles, rgb, clamped, gfl);
+    int64_t K = 0;
+    for (int64_t i = 0; i < n; ++i) K += tiles[i];
+    int64_t ntile = (int64_t)gx * ((H + tile_h - 1) / tile_h);
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(K + 1));
+    uint32_t* vals = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(K + 1));
+    uint32_t* ranges = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * ntile + 2));
+    orc_sort(n, gx, (H + tile_h - 1) / tile_h, 0, 0, rect, tiles, dbits, K, keys, vals, ranges);
+
+    /* 2D gradients: du dv da db dc do dr dg db */
+    double* G2 = (double*)calloc((size_t)n * 9 + 1, sizeof(double));
+    const double* bg = cam + CAM_BG;
+    const double a_min = 1.0 / 255.0;
+    uint32_t* lid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(K + 1));
+    double* lal = (double*)malloc(sizeof(double) * (size_t)(K + 1));
+    double* lT = (double*)malloc(sizeof(double) * (size_t)(K + 1));
+    double* lep = (double*)malloc(sizeof(double) * (size_t)(K + 1));
+    uint8_t* lcl = (uint8_t*)malloc((size_t)(K + 1));
+    for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+        int px = (int)(pix % W), py = (int)(pix / W);
+        int64_t tile = (int64_t)(py / tile_h) * gx + px / tile_w;
+        uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+        double T = 1.0;
+        int cnt = 0;
+        for (uint32_t k = s; k < e; ++k) {
+            uint32_t id = vals[k];
+            double dx = uv[2 * id] - px, dy = uv[2 * id + 1] - py;
+            double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2];
+            double p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+            double ep = exp(p);
+            double al = (double)opac[id] * ep;
+            uint8_t cl = 0;
+            if (al > 0.99) { al = 0.99; cl = 1; }
+            if (al < a_min) continue;
+            double test_T = T * (1.0 - al);
+            if (test_T < 1e-4) break;
+            lid[cnt] = id; lal[cnt] = al; lT[cnt] = T; lep[cnt] = ep; lcl[cnt] = cl;
+            ++cnt;
+            T = test_T;
+        }
+        double Tf = T;
+        double g[3] = { dL_drgb[pix], dL_drgb[(int64_t)W * H + pix], dL_drgb[2 * (int64_t)W * H + pix] };
+        double gT = dL_dT ? dL_dT[pix] : 0.0;
+        double tail = Tf * (bg[0] * g[0] + bg[1] * g[1] + bg[2] * g[2]) + Tf * gT;
+        double S = 0.0; /* <S_k, g> */
+        for (int j = cnt - 1; j >= 0; --j) {
+            uint32_t id = lid[j];
+            double al = lal[j], Tk = lT[j];
+            double cg = rgb[3 * id] * g[0] + rgb[3 * id + 1] * g[1] + rgb[3 * id + 2] * g[2];
+            for (int ch = 0; ch < 3; ++ch) G2[9 * id + 6 + ch] += al * Tk * g[ch];
+            double dal = Tk * cg - (S + tail) / (1.0 - al);
+            S += cg * al * Tk;
+            if (lcl[j]) continue;
+            double dx = uv[2 * id] - px, dy = uv[2 * id + 1] - py;
+            double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2];
+            double dp = dal * al;
+            G2[9 * id + 5] += dal * lep[j];
+            G2[9 * id + 2] += dp * (-0.5 * dx * dx);
+            G2[9 * id + 3] += dp * (-dx * dy);
+            G2[9 * id + 4] += dp * (-0.5 * dy * dy);
+            G2[9 * id + 0] += dp * (-(a * dx + b * dy));
+            G2[9 * id + 1] += dp * (-(b * dx + c * dy));
+        }
+    }
+
+    /* per Gaussian chain rule */
+    const double* Rw = cam + CAM_R;
+    double fx = cam[CAM_FX], fy = cam[CAM_FY];
+    double limx = 1.3 * (W / (2.0 * fx)), limy = 1.3 * (H / (2.0 * fy));
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) { g_means[3 * i + k] = 0; g_scales[3 * i + k] = 0; }
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = 0;
+        g_opac[i] = 0;
+        for (int k = 0; k < Ksh * 3; ++k) g_sh[i * Ksh * 3 + k] = 0;
+        if (g2d) for (int k = 0; k < 9; ++k) g2d[9 * i + k] = G2[9 * i + k];
+        if (tiles[i] == 0) continue;
+        double* G = G2 + 9 * i;
+        double mu[3] = { means[3 * i], means[3 * i + 1], means[3 * i + 2] };
+        double t[3];
+        for (int r = 0; r < 3; ++r)
+            t[r] = ((Rw[r * 3 + 0] * mu[0] + Rw[r * 3 + 1] * mu[1]) + Rw[r * 3 + 2] * mu[2]) + cam[CAM_T + r];
+        double s[3] = { scales[3 * i], scales[3 * i + 1], scales[3 * i + 2] };
+        double q[4] = { quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3] };
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qh[4] = { q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn };
+        double R[9], Sig[9];
+        orc_quat_to_rot(qh, R);
+        orc_cov3d(s, q, Sig);
+        double tz = t[2];
+        double rx = t[0] / tz, ry = t[1] / tz;
+        int clx = 0, cly = 0;
+        if (rx < -limx) { rx = -limx; clx = 1; } if (rx > limx) { rx = limx; clx = 1; }
+        if (ry < -limy) { ry = -limy; cly = 1; } if (ry > limy) { ry = limy; cly = 1; }
+        double J[6] = { fx / tz, 0.0, -fx * rx / tz, 0.0, fy / tz, -fy * ry / tz };
+        double Tm[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += J[r * 3 + k] * Rw[k * 3 + c2];
+                Tm[r * 3 + c2] = acc;
+            }
+        double C[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c2 = 0; c2 < 2; ++c2) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) acc += Tm[r * 3 + k] * Sig[k * 3 + l] * Tm[c2 * 3 + l];
+                C[r * 2 + c2] = acc;
+            }
+        double s00 = C[0] + 0.3, s01 = C[1], s11 = C[3] + 0.3;
+        double D = s00 * s11 - s01 * s01, D2 = D * D;
+        double ga = G[2], gb = G[3], gc = G[4];
+        double g00 = ga * (-s11 * s11 / D2) + gb * (s01 * s11 / D2) + gc * (1.0 / D - s00 * s11 / D2);
+        double g11 = ga * (1.0 / D - s11 * s00 / D2) + gb * (s01 * s00 / D2) + gc * (-s00 * s00 / D2);
+        double g01 = ga * (2.0 * s01 * s11 / D2) + gb * (-1.0 / D - 2.0 * s01 * s01 / D2) +
+                     gc * (2.0 * s01 * s00 / D2);
+        double Gm[4] = { g00, 0.5 * g01, 0.5 * g01, g11 };
+        /* dL/dSigma = T^T G T ; dL/dT = 2 G T Sigma */
+        double dSig[9], dT[6], GT[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c2 = 0; c2 < 3; ++c2)
+                GT[r * 3 + c2] = Gm[r * 2 + 0] * Tm[c2] + Gm[r * 2 + 1] * Tm[3 + c2];
+        for (int r = 0; r < 3; ++r)
+            for (int c2 = 0; c2 < 3; ++c2)
+                dSig[r * 3 + c2] = Tm[r] * GT[c2] + Tm[3 + r] * GT[3 + c2];
+        for (int r = 0; r < 2; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += GT[r * 3 + k] * Sig[k * 3 + c2];
+                dT[r * 3 + c2] = 2.0 * acc;
+            }
+        double dJ[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += dT[r * 3 + k] * Rw[c2 * 3 + k];
+                dJ[r * 3 + c2] = acc;
+            }
+        double dt[3] = { 0, 0, 0 };
+        double drx_dtx = clx ? 0.0 : 1.0 / tz, drx_dtz = clx ? 0.0 : -t[0] / (tz * tz);
+        double dry_dty = cly ? 0.0 : 1.0 / tz, dry_dtz = cly ? 0.0 : -t[1] / (tz * tz);
+        dt[2] += dJ[0] * (-fx / (tz * tz)) + dJ[4] * (-fy / (tz * tz));
+        dt[2] += dJ[2] * (fx * rx / (tz * tz) - fx / tz * drx_dtz);
+        dt[2] += dJ[5] * (fy * ry / (tz * tz) - fy / tz * dry_dtz);
+        dt[0] += dJ[2] * (-fx / tz * drx_dtx);
+        dt[1] += dJ[5] * (-fy / tz * dry_dty);
+        /* projected mean */
+        dt[0] += G[0] * fx / tz;
+        dt[1] += G[1] * fy / tz;
+        dt[2] += G[0] * (-fx * t[0] / (tz * tz)) + G[1] * (-fy * t[1] / (tz * tz));
+        for (int k = 0; k < 3; ++k)
+            g_means[3 * i + k] += Rw[0 * 3 + k] * dt[0] + Rw[1 * 3 + k] * dt[1] + Rw[2 * 3 + k] * dt[2];
+        /* Sigma = M M^T, M = R diag(s) */
+        double dM[9], M[9];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) M[r * 3 + k] = R[r * 3 + k] * s[k];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) {
+                double acc = 0;
+                for (int l = 0; l < 3; ++l) acc += dSig[r * 3 + l] * M[l * 3 + k];
+                dM[r * 3 + k] = 2.0 * acc;
+            }
+        double dR[9];
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0;
+            for (int r = 0; r < 3; ++r) acc += dM[r * 3 + k] * R[r * 3 + k];
+            g_scales[3 * i + k] = acc;
+            for (int r = 0; r < 3; ++r) dR[r * 3 + k] = dM[r * 3 + k] * s[k];
+        }
+        double w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+        double Rw_[9] = { 0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0 };
+        double Rx_[9] = { 0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x };
+        double Ry_[9] = { -4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y };
+        double Rz_[9] = { -4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0 };
+        double dqh[4] = { 0, 0, 0, 0 };
+        for (int k = 0; k < 9; ++k) {
+            dqh[0] += dR[k] * Rw_[k]; dqh[1] += dR[k] * Rx_[k];
+            dqh[2] += dR[k] * Ry_[k]; dqh[3] += dR[k] * Rz_[k];
+        }
+        double proj = qh[0] * dqh[0] + qh[1] * dqh[1] + qh[2] * dqh[2] + qh[3] * dqh[3];
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = (dqh[k] - qh[k] * proj) / qn;
+        g_opac[i] = G[5];
+        /* SH colour */
+        double d[3] = { mu[0] - cam[CAM_POS], mu[1] - cam[CAM_POS + 1], mu[2] - cam[CAM_POS + 2] };
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double dir[3] = { d[0] / dn, d[1] / dn, d[2] / dn };
+        double Y[16], dY[16][3];
+        sh_grad(sh_degree, dir, Y, dY);
+        double gdir[3] = { 0, 0, 0 };
+        for (int ch = 0; ch < 3; ++ch) {
+            if (clamped[3 * i + ch]) continue;
+            double gr = G[6 + ch];
+            for (int k = 0; k < Ksh; ++k) {
+                g_sh[(i * Ksh + k) * 3 + ch] = Y[k] * gr;
+                double shv = sh[(i * Ksh + k) * 3 + ch];
+                for (int c2 = 0; c2 < 3; ++c2) gdir[c2] += gr * shv * dY[k][c2];
+            }
+        }
+        double pr = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+        for (int k = 0; k < 3; ++k) g_means[3 * i + k] += (gdir[k] - dir[k] * pr) / dn;
+    }
+    free(uv); free(depth); free(dbits); free(conic); free(radius); free(rect); free(tiles);
+    free(rgb); free(clamped); free(gfl); free(keys); free(vals); free(ranges); free(G2);
+    free(lid); free(lal); free(lT); free(lep); free(lcl);
 }
