@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--tile", default="16x16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="only run warm-up + steps of the Local-GS pipeline (for ncu), no report")
+    p.add_argument("--views", type=int, default=8, help="views of the outdoor workload (profiling)")
+    p.add_argument("--mode", default="localgs", choices=["localgs", "plain"])
     return p.parse_args()
 
 
@@ -224,7 +228,17 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     tile = tuple(int(x) for x in args.tile.split("x"))
     scene, cams = scenes.outdoor()
+    cams = cams[:args.views]
     g = lgs.to_device(scene, dev)
+    if args.profile:
+        probe = lgs.render(g, cams, tile=tile)
+        pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
+        del probe
+        cfg = lgs.config(tile, args.mode)
+        for _ in range(args.warmup + args.steps):
+            pipe.step(cfg)
+        torch.cuda.synchronize()
+        return
     cfg_l = lgs.config(tile, "localgs")
     cfg_p = lgs.config(tile, "plain")
 
