@@ -31,7 +31,8 @@
  *  - Arrays loaded as float4 (marked "16-B aligned") must start on a 16-byte
  *    boundary, otherwise LGS_ERR_ALIGN.
  *  - No C++ exception crosses the ABI. The library holds no mutable global
- *    state.
+ *    state, except the static scratch array of lgs_sort_static and its cached
+ *    per-device address.
  *
  * Multi-view batches: n_views cameras (1..LGS_MAX_VIEWS) are processed in one
  * call. Per-(view, Gaussian) arrays are view-major, index v*N + i. Tile ids are
@@ -184,6 +185,34 @@ lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, i
                     const lgs_config* cfg, int64_t capacity, uint64_t* keys, uint32_t* vals,
                     uint32_t* ranges, void* workspace, size_t workspace_bytes, int64_t* d_status,
                     void* stream);
+
+/* lgs_sort without a workspace argument. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at all --
+ * for example a plugin inside a host engine that owns every device allocation
+ * and forbids third-party code from calling cudaMalloc, or a real-time render
+ * loop that must never enter an allocator after start-up -- and so cannot hand
+ * lgs_sort a workspace. Its scratch is a file-scope __device__ array of
+ * LGS_SORT_STATIC_BYTES that every GPU loading the library holds until exit;
+ * the call itself allocates nothing (no cudaMalloc, no allocating library
+ * routine).
+ * Limits: n * n_views <= LGS_SORT_STATIC_MAX_ENTRIES and capacity <=
+ * LGS_SORT_STATIC_MAX_INSTANCES, otherwise LGS_ERR_UNSUPPORTED is returned
+ * before anything is enqueued. Other arguments, outputs and errors are those of
+ * lgs_sort.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the one array, which keeps the previous call's
+ * contents (nothing in it needs to start at zero: every word the sort reads is
+ * written earlier in the same call), so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
+#define LGS_SORT_STATIC_MAX_ENTRIES (1ll << 18)
+#define LGS_SORT_STATIC_MAX_INSTANCES (1ll << 20)
+#define LGS_SORT_STATIC_BYTES (14ull << 20)
+lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams,
+                           int32_t n_views, const lgs_config* cfg, int64_t capacity,
+                           uint64_t* keys, uint32_t* vals, uint32_t* ranges, int64_t* d_status,
+                           void* stream);
 
 /* Stage 3, render (Sec. II-A render kernel; Local-GS Sec. III or the plain
  * per-pixel kernel, cfg->mode). Per pixel, front to back over its tile's list:

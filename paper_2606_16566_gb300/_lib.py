@@ -21,6 +21,8 @@ LGS_ERR_TIMEOUT = 6
 LGS_ERR_CUDA = 7
 
 LGS_MAX_VIEWS = 64
+SORT_STATIC_MAX_ENTRIES = 1 << 18
+SORT_STATIC_MAX_INSTANCES = 1 << 20
 LGS_STATUS_WORDS = 8
 ST_CODE, ST_DETAIL, ST_NUM_INSTANCES, ST_NONFINITE, ST_PAIRS, ST_QUEUE, ST_QUEUE_BWD, ST_SPARE = range(8)
 
@@ -70,6 +72,10 @@ SIGNATURES = {
                                   ctypes.POINTER(lgs_camera), ctypes.c_int32,
                                   ctypes.POINTER(lgs_config), ctypes.c_int64, _vp, _vp, _vp, _vp,
                                   ctypes.c_size_t, _vp, _vp]),
+    "lgs_sort_static": (ctypes.c_int32, [ctypes.POINTER(lgs_pre_out), ctypes.c_int64,
+                                         ctypes.POINTER(lgs_camera), ctypes.c_int32,
+                                         ctypes.POINTER(lgs_config), ctypes.c_int64, _vp, _vp, _vp,
+                                         _vp, _vp]),
     "lgs_render_fwd": (ctypes.c_int32, [ctypes.POINTER(lgs_pre_out), _vp, _vp,
                                         ctypes.POINTER(lgs_camera), ctypes.c_int32,
                                         ctypes.POINTER(lgs_config), _vp, _vp, _vp, _vp, _vp]),

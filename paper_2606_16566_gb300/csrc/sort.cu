@@ -17,6 +17,8 @@
 #include "common.cuh"
 #include "host.h"
 
+#include <mutex>
+
 namespace lgs {
 
 constexpr int SCAN_THREADS = 256;
@@ -324,7 +326,20 @@ struct SortWs {
     uint32_t* digit_total; // [256]
 };
 
-inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bytes of the sort workspace for m entries and an instance capacity
+// (usable in constant expressions).
+constexpr size_t sort_ws_bytes(int64_t m, int64_t capacity) {
+    const int64_t nscan = (m + SCAN_TILE - 1) / SCAN_TILE;
+    const int64_t nb = (capacity + SORT_TILE - 1) / SORT_TILE;
+    return align_up(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1)) +
+           align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1)) +
+           align_up(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1)) +
+           align_up(sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1)) +
+           align_up(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1)) +
+           align_up(sizeof(uint32_t) * RADIX);
+}
 
 inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws) {
     const int64_t nscan = (m + SCAN_TILE - 1) / SCAN_TILE;
@@ -429,4 +444,60 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
     sort_ws_layout(m, capacity, static_cast<char*>(workspace), &ws);
     return sort_enqueue(pre, n, &vs, capacity, keys, vals, ranges, &ws, d_status,
                             static_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------------ static scratch variant
+// lgs_sort_static: lgs_sort for callers that cannot allocate device memory.
+// Its scratch lives in a file-scope device array, so every GPU that loads the
+// library holds LGS_SORT_STATIC_BYTES of it until the process exits.
+namespace lgs {
+constexpr size_t kSortStaticBytes =
+    sort_ws_bytes(LGS_SORT_STATIC_MAX_ENTRIES, LGS_SORT_STATIC_MAX_INSTANCES);
+static_assert(kSortStaticBytes <= (size_t)LGS_SORT_STATIC_BYTES,
+              "LGS_SORT_STATIC_BYTES must cover the workspace at the stated maxima");
+}  // namespace lgs
+
+static __device__ __align__(256) unsigned char g_sort_static_scratch[LGS_SORT_STATIC_BYTES];
+
+// Device address of the array on the current device. In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+static lgs_status sort_static_scratch(void** out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void* ptr[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LGS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sort_static_scratch) != cudaSuccess || !p) return LGS_ERR_CUDA;
+        ptr[dev] = p;
+    }
+    *out = ptr[dev];
+    return LGS_OK;
+}
+
+extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams,
+                                      int32_t n_views, const lgs_config* cfg, int64_t capacity,
+                                      uint64_t* keys, uint32_t* vals, uint32_t* ranges,
+                                      int64_t* d_status, void* stream) {
+    if (!pre || !keys || !vals || !ranges || !d_status) return LGS_ERR_ARG;
+    if (n < 0 || capacity < 0) return LGS_ERR_ARG;
+    Views vs;
+    lgs_status st = make_views(cams, n_views, cfg, &vs);
+    if (st != LGS_OK) return st;
+    const int64_t m = n * (int64_t)n_views;
+    if (m > LGS_SORT_STATIC_MAX_ENTRIES || capacity > LGS_SORT_STATIC_MAX_INSTANCES)
+        return LGS_ERR_UNSUPPORTED;
+    if (!pre->tiles || !pre->rect || !pre->depth) return LGS_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u))
+        return LGS_ERR_ALIGN;
+    void* scratch = nullptr;
+    st = sort_static_scratch(&scratch);
+    if (st != LGS_OK) return st;
+    SortWs ws;
+    sort_ws_layout(m, capacity, static_cast<char*>(scratch), &ws);
+    return sort_enqueue(pre, n, &vs, capacity, keys, vals, ranges, &ws, d_status,
+                        static_cast<cudaStream_t>(stream));
 }

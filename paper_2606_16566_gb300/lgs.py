@@ -150,6 +150,23 @@ def sort(pre: PreOut, n, cams, cfg, capacity, keys=None, vals=None, ranges=None,
     return keys, vals, ranges
 
 
+def sort_static(pre: PreOut, n, cams, cfg, capacity, keys=None, vals=None, ranges=None,
+                status=None, stream=None):
+    """lgs_sort_static: the sort with the library's static scratch (no workspace)."""
+    carr = cameras(cams)
+    dev = pre.xy.device
+    keys = keys if keys is not None else torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    vals = vals if vals is not None else torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    ranges = ranges if ranges is not None else torch.empty((n_tiles(cams, cfg), 2), dtype=torch.int32,
+                                                           device=dev)
+    status = status if status is not None else new_status(dev)
+    ps = pre.struct()
+    L.check(L.load().lgs_sort_static(ctypes.byref(ps), n, carr, len(carr), ctypes.byref(cfg), capacity,
+                                     _ptr(keys), _ptr(vals), _ptr(ranges), _ptr(status),
+                                     _stream(stream)), "lgs_sort_static")
+    return keys, vals, ranges
+
+
 def render_fwd(pre: PreOut, vals, ranges, cams, cfg, rgb=None, final_T=None, n_contrib=None,
                status=None, stream=None):
     carr = cameras(cams)
