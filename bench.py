@@ -164,7 +164,6 @@ class Pipeline:
         self.status = lgs.new_status(dev)
         self.pre = lgs.PreOut.empty(self.m, dev)
         self.capacity = capacity
-        self.keys = torch.empty(capacity, dtype=torch.int64, device=dev)
         self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
         self.ranges = torch.empty((lgs.n_tiles(cams, lgs.config(tile)), 2), dtype=torch.int32, device=dev)
         self.ws = torch.empty(lgs.sort_workspace_size(self.m, capacity), dtype=torch.uint8, device=dev)
@@ -178,8 +177,9 @@ class Pipeline:
         self.lgs.preprocess(self.g, self.cams, cfg, out=self.pre, status=self.status)
 
     def stage_sort(self, cfg):
-        self.lgs.sort(self.pre, self.n, self.cams, cfg, self.capacity, self.keys, self.vals, self.ranges,
-                      self.ws, self.status)
+        # the render consumes values and tile ranges; the 64-bit keys are not materialised
+        self.lgs.sort(self.pre, self.n, self.cams, cfg, self.capacity, None, self.vals, self.ranges,
+                      self.ws, self.status, with_keys=False)
 
     def stage_render(self, cfg):
         self.lgs.render_fwd(self.pre, self.vals, self.ranges, self.cams, cfg, self.rgb, self.T, self.nc,
@@ -191,13 +191,15 @@ class Pipeline:
         self.stage_render(cfg)
 
     def launches(self):
+        """Kernels of one step: preprocess; depth keys + 4 entry passes (3 kernels
+        each); gather + 3 scan kernels; emission; tile-id passes; ranges; render."""
         from math import ceil
         nt = self.ranges.shape[0]
         bits = 0
         while (1 << bits) < nt:
             bits += 1
-        passes = ceil((32 + bits) / 8)
-        return 1 + 3 + 1 + 3 * passes + 1 + 1
+        tile_passes = ceil(bits / 8)
+        return 1 + 1 + 4 * 3 + 1 + 3 + 1 + 3 * tile_passes + 1 + 1
 
 
 def time_steps(pipe, cfg, steps, flush):

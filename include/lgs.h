@@ -174,11 +174,12 @@ size_t lgs_sort_workspace_size(int64_t m, int64_t capacity);
  * surviving primitives across intersecting tiles into 64-bit key-value pairs,
  * which are sorted by GPU radix sort to produce ... tile ranges"):
  * exclusive scan of tiles, emission of key = (tile_id << 32) | bits(depth) and
- * value = v*N + i in Gaussian order (tiles row-major inside the rect), stable
- * LSD radix sort on the 32 + ceil(log2(tiles)) significant key bits, and
- * per-tile ranges [start, end) (0,0 for empty tiles).
- * keys [capacity] u64, vals [capacity] u32, ranges [n_tiles_total,2] u32 (all
- * device, caller-owned). K is written to d_status[LGS_ST_NUM_INSTANCES]; if
+ * value = v*N + i in Gaussian order (tiles row-major inside the rect), a stable
+ * radix sort by key (ties keep emission order), and per-tile ranges
+ * [start, end) (0,0 for empty tiles).
+ * keys [capacity] u64 (may be NULL: the sorted keys are then not written),
+ * vals [capacity] u32, ranges [n_tiles_total,2] u32 (all device, caller-owned,
+ * keys and ranges 8-B aligned). K is written to d_status[LGS_ST_NUM_INSTANCES]; if
  * K > capacity nothing is sorted, d_status records LGS_ERR_CAPACITY with K as
  * detail and ranges are left empty. capacity must be < 2^32. */
 lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, int32_t n_views,
@@ -208,7 +209,7 @@ lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, i
  * caller. */
 #define LGS_SORT_STATIC_MAX_ENTRIES (1ll << 18)
 #define LGS_SORT_STATIC_MAX_INSTANCES (1ll << 20)
-#define LGS_SORT_STATIC_BYTES (14ull << 20)
+#define LGS_SORT_STATIC_BYTES (20ull << 20)
 lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams,
                            int32_t n_views, const lgs_config* cfg, int64_t capacity,
                            uint64_t* keys, uint32_t* vals, uint32_t* ranges, int64_t* d_status,

@@ -1,6 +1,518 @@
-// backward.cu -- adjoint of the render and preprocess stages.
+// backward.cu -- adjoint of the render and preprocess stages (the paper covers
+// inference only; this is the reverse-mode derivative of the same forward map,
+// for L = <dL/drgb, rgb> + <dL/dT, final_T>).
+//
+// render_bwd_localgs: one CTA per tile, the tile list walked back to front from
+// the largest contributor count in the tile. Gaussians are staged and hoisted
+// exactly as in the forward kernel (same V, same warp mask, same FP32
+// arithmetic), so every alpha >= 1/255 decision is reproduced bit for bit; a
+// lane takes part for list positions <= its stored n_contrib. Per pixel the
+// transmittance before each Gaussian is recovered as T / (1 - alpha) from the
+// stored final T, and
+//   dL/drgb_k  = alpha_k T_k g
+//   dL/dalpha_k = T_k <rgb_k - A_k, g> - T_f (<bg, g> + gT) / (1 - alpha_k)
+// with A_k the colour behind k normalised by T_{k+1} (A <- alpha rgb + (1-alpha) A).
+// Since ln(alpha) = V . B_local (hoist transform), dL/dV = (dL/dalpha alpha) B_local:
+// six hoisted gradients plus three colour gradients per pair, summed over the
+// warp's 32 pixels with a transposed shuffle reduction (9 values in 14
+// shuffles), over the CTA's 8 warps with shared-memory atomics, and mapped
+// once per (Gaussian, tile) through the transpose of the hoist Jacobian to
+// dL/d(a, b, c, o, u, v) before one global atomic per component.
+//
+// preprocess_bwd: one thread per Gaussian looping over the views, chain rule
+// through conic inversion (dL/dSigma' = -Q dL/dQ Q), Sigma' = M M^T + 0.3 I with
+// M = J W R diag(s), the EWA Jacobian J(t) (zero slope in a clamped direction
+// ratio), the projected mean, quaternion normalisation and the SH colour
+// (Cartesian basis polynomials, gradient projected onto the unit sphere).
 #include "common.cuh"
 #include "host.h"
+
+namespace lgs {
+
+constexpr int BWD_BATCH = 256;
+constexpr float LOG2E_B = 1.4426950408889634f;
+constexpr float LOG2_ALPHA_MIN_B = -7.9943534368588580f;
+constexpr float LN255_B = 5.5412635451584258f;
+
+struct BwdParams {
+    const float4* xy;
+    const float4* conic;
+    const float4* rgb;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const float* final_T;
+    const uint32_t* n_contrib;
+    const float* dL_drgb;
+    const float* dL_dT;
+    float* g_xy;      // [M,2]
+    float* g_conic;   // [M,4]
+    float* g_rgb;     // [M,3]
+};
+
+__device__ __forceinline__ float ex2_approx_b(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Identical to the forward kernel's warp mask (conservative tight box).
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_mask_b(float a, float b, float c, float o, float mux,
+                                                float muy, int X0, int Y0) {
+    constexpr int ROWS = TH / 8;
+    float tau = 2.f * (LN255_B + __logf(o));
+    tau = fmaf(tau, 1.001f, 0.02f);
+    if (!(tau > 0.f)) return 0u;
+    const float det = fmaf(a, c, -b * b);
+    if (!(det > 0.f)) return 0xffu;
+    const float ct = c * tau, at = a * tau;
+    const float xr = sqrtf(ct / det);
+    float x0 = (float)X0 - mux, x1 = (float)(X0 + TW - 1) - mux;
+    if (x1 < -xr || x0 > xr) return 0u;
+    x0 = fmaxf(x0, -xr);
+    x1 = fminf(x1, xr);
+    const float dy = sqrtf(at / det);
+    float ymax, ymin;
+    if (-b * dy < a * x0)      ymax = (-b * x0 + sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
+    else if (-b * dy > a * x1) ymax = (-b * x1 + sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
+    else                       ymax = dy;
+    if (b * dy < a * x0)       ymin = (-b * x0 - sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
+    else if (b * dy > a * x1)  ymin = (-b * x1 - sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
+    else                       ymin = -dy;
+    const float ylo = fmaxf((float)Y0, muy + ymin - 0.015625f);
+    const float yhi = fminf((float)(Y0 + TH - 1), muy + ymax + 0.015625f);
+    if (!(ylo <= yhi)) return 0u;
+    const int ys = (int)ceilf(ylo), ye = (int)floorf(yhi);
+    if (ys > ye) return 0u;
+    const int ws = (ys - Y0) / ROWS, we = (ye - Y0) / ROWS;
+    return ((1u << (we - ws + 1)) - 1u) << ws;
+}
+
+// Sum of v[0..7] over the warp: lane L ends up holding the total of value
+// ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1), i.e. lanes 4i..4i+3
+// hold value i. Each halving step exchanges only the half a lane gives away.
+__device__ __forceinline__ float warp_sum8_transposed(float v[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h16 ? v[i] : v[i + 4];
+        const float keep = h16 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float b2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h8 ? a[i] : a[i + 2];
+        const float keep = h8 ? a[i + 2] : a[i];
+        b2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = h4 ? b2[0] : b2[1];
+    float c1 = (h4 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, 2);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, 1);
+    return c1;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs) {
+    __shared__ float4 sV[BWD_BATCH];
+    __shared__ float2 sDE[BWD_BATCH];
+    __shared__ float4 sC[BWD_BATCH];
+    __shared__ uint8_t sM[BWD_BATCH];
+    __shared__ uint32_t sId[BWD_BATCH];
+    __shared__ float sG[BWD_BATCH][9];
+    __shared__ uint32_t sLast[8];
+
+    const uint32_t tile = blockIdx.x;
+    const int view = view_of_tile(vs, tile);
+    const ViewRec& c = vs.v[view];
+    const uint32_t lt = tile - c.tile_off;
+    const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = lane % TW, ly = warp * (TH / 8) + lane / TW;
+    const int px = X0 + lx, py = Y0 + ly;
+    const bool inside = px < c.W && py < c.H;
+    const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
+    const float xl = (float)lx - 0.5f * (TW - 1), yl = (float)ly - 0.5f * (TH - 1);
+    const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
+    const uint2 r = p.ranges[tile];
+
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, tail = 0.f;
+    uint32_t last = 0;
+    if (inside) {
+        const int64_t plane = (int64_t)c.W * c.H;
+        const int64_t pix = (int64_t)py * c.W + px;
+        const float* gr = p.dL_drgb + 3 * (int64_t)c.pix_off;
+        g0 = gr[pix];
+        g1 = gr[plane + pix];
+        g2 = gr[2 * plane + pix];
+        T = p.final_T[c.pix_off + pix];
+        last = p.n_contrib[c.pix_off + pix];
+        const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
+        tail = T * (c.bg[0] * g0 + c.bg[1] * g1 + c.bg[2] * g2 + gT);
+    }
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+    uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) sLast[warp] = wlast;
+    __syncthreads();
+    uint32_t tlast = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tlast = max(tlast, sLast[w]);
+
+    for (int end = (int)tlast; end > 0; end -= BWD_BATCH) {
+        const int begin = max(0, end - BWD_BATCH);
+        const int nb = end - begin;
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            const uint32_t pos = (uint32_t)(begin + threadIdx.x);
+            const uint32_t id = p.vals[r.x + pos];
+            const float4 xy = p.xy[id];
+            const float4 co = p.conic[id];
+            const float4 col = p.rgb[id];
+            const float dx = __fadd_rn(xy.x - Ox, xy.z);
+            const float dy = __fadd_rn(xy.y - Oy, xy.w);
+            const float Dn = fmaf(co.x, dx, co.y * dy);
+            const float En = fmaf(co.y, dx, co.z * dy);
+            const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
+            sV[threadIdx.x] = make_float4(-0.5f * LOG2E_B * co.x, -LOG2E_B * co.y, -0.5f * LOG2E_B * co.z,
+                                          fmaf(Fn, LOG2E_B, __log2f(co.w)));
+            sDE[threadIdx.x] = make_float2(Dn * LOG2E_B, En * LOG2E_B);
+            sC[threadIdx.x] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
+            sM[threadIdx.x] = (uint8_t)warp_mask_b<TW, TH>(co.x, co.y, co.z, co.w, xy.x + xy.z,
+                                                           xy.y + xy.w, X0, Y0);
+            sId[threadIdx.x] = id;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sG[threadIdx.x][k] = 0.f;
+        }
+        __syncthreads();
+        if (wlast > (uint32_t)begin) {
+            for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+                const int jj = c0 + lane;
+                uint32_t bits = __ballot_sync(0xffffffffu, jj < nb && ((sM[jj] >> warp) & 1u) &&
+                                                               (uint32_t)(begin + jj) < wlast);
+                while (bits) {
+                    const int k = 31 - __clz(bits);
+                    bits &= ~(1u << k);
+                    const int g = c0 + k;
+                    const float4 V = sV[g];
+                    const float2 DE = sDE[g];
+                    const float4 col = sC[g];
+                    const uint32_t pos = __float_as_uint(col.w);
+                    const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
+                                     fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
+                    const float e2 = ex2_approx_b(pw);
+                    const float al = fminf(0.99f, e2);
+                    float v[8];
+                    float gb = 0.f;
+                    if (pos <= last && pw >= LOG2_ALPHA_MIN_B) {
+                        const float om = 1.f - al;
+                        const float Tk = T / om;
+                        const float w = al * Tk;
+                        v[5] = w * g0;
+                        v[6] = w * g1;
+                        gb = w * g2;
+                        const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
+                        const float dal = Tk * cg - tail / om;
+                        A0 = fmaf(al, col.x - A0, A0);
+                        A1 = fmaf(al, col.y - A1, A1);
+                        A2 = fmaf(al, col.z - A2, A2);
+                        T = Tk;
+                        const float dp = (e2 > 0.99f) ? 0.f : dal * al;   // natural-log power
+                        v[0] = dp * bx2;
+                        v[1] = dp * bxy;
+                        v[2] = dp * by2;
+                        v[3] = dp * xl;
+                        v[4] = dp * yl;
+                        v[7] = dp;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+                    }
+                    const float s8 = warp_sum8_transposed(v);
+                    const float s9 = warp_sum(gb);
+                    if ((lane & 3) == 0) atomicAdd(&sG[g][lane >> 2], s8);
+                    if (lane == 0) atomicAdd(&sG[g][8], s9);
+                }
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            // hoisted gradients (A, B, C, D, E, F in natural-log units) -> (a, b, c, ln o, Dx, Dy)
+            const int t = threadIdx.x;
+            const float gA = sG[t][0], gB = sG[t][1], gC = sG[t][2], gD = sG[t][3], gE = sG[t][4];
+            const float gF = sG[t][7];
+            const uint32_t id = sId[t];
+            const float4 xy = p.xy[id];
+            const float4 co = p.conic[id];
+            const float dx = __fadd_rn(xy.x - Ox, xy.z);
+            const float dy = __fadd_rn(xy.y - Oy, xy.w);
+            const float Dn = fmaf(co.x, dx, co.y * dy);
+            const float En = fmaf(co.y, dx, co.z * dy);
+            const float ga = -0.5f * gA + dx * gD - 0.5f * dx * dx * gF;
+            const float gbb = -gB + dy * gD + dx * gE - dx * dy * gF;
+            const float gc = -0.5f * gC + dy * gE - 0.5f * dy * dy * gF;
+            const float go = gF / co.w;
+            const float gdx = co.x * gD + co.y * gE - Dn * gF;
+            const float gdy = co.y * gD + co.z * gE - En * gF;
+            if (ga != 0.f || gbb != 0.f || gc != 0.f || go != 0.f || gdx != 0.f || gdy != 0.f) {
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 0, ga);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 1, gbb);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 2, gc);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 3, go);
+                atomicAdd(p.g_xy + 2 * (int64_t)id + 0, gdx);
+                atomicAdd(p.g_xy + 2 * (int64_t)id + 1, gdy);
+            }
+            const float gr0 = sG[t][5], gr1 = sG[t][6], gr2 = sG[t][8];
+            if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 0, gr0);
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 1, gr1);
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 2, gr2);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ preprocess adjoint
+struct PreBwdParams {
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* sh;
+    int64_t n;
+    const float4* conic;   // forward conic (a, b, c, o)
+    const uint32_t* tiles;
+    const uint8_t* flags;
+    const float* g_xy;
+    const float* g_conic;
+    const float* g_rgb;
+    float* d_means;
+    float* d_scales;
+    float* d_quats;
+    float* d_opac;
+    float* d_sh;
+};
+
+// Basis value and Cartesian gradient of the real SH polynomials (Condon-Shortley
+// phase, index l^2 + l + m) at a unit direction.
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* Y, float (*dY)[3]) {
+    constexpr float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    Y[0] = C0; dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+    if (DEG >= 1) {
+        Y[1] = -C1 * y; dY[1][0] = 0.f; dY[1][1] = -C1; dY[1][2] = 0.f;
+        Y[2] = C1 * z;  dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = C1;
+        Y[3] = -C1 * x; dY[3][0] = -C1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    }
+    if (DEG >= 2) {
+        constexpr float a = 1.0925484305920792f, b = 0.31539156525252005f, e = 0.5462742152960396f;
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = a * x * y;   dY[4][0] = a * y;  dY[4][1] = a * x;  dY[4][2] = 0.f;
+        Y[5] = -a * y * z;  dY[5][0] = 0.f;    dY[5][1] = -a * z; dY[5][2] = -a * y;
+        Y[6] = b * (2.f * zz - xx - yy); dY[6][0] = -2.f * b * x; dY[6][1] = -2.f * b * y; dY[6][2] = 4.f * b * z;
+        Y[7] = -a * x * z;  dY[7][0] = -a * z; dY[7][1] = 0.f;    dY[7][2] = -a * x;
+        Y[8] = e * (xx - yy); dY[8][0] = 2.f * e * x; dY[8][1] = -2.f * e * y; dY[8][2] = 0.f;
+    }
+    if (DEG >= 3) {
+        constexpr float c1 = -0.5900435899266435f, c2 = 2.890611442640554f, c3 = -0.4570457994644658f,
+                        c4 = 0.3731763325901154f, c6 = 1.445305721320277f;
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[9] = c1 * y * (3.f * xx - yy);
+        dY[9][0] = 6.f * c1 * x * y; dY[9][1] = c1 * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+        Y[10] = c2 * x * y * z;
+        dY[10][0] = c2 * y * z; dY[10][1] = c2 * x * z; dY[10][2] = c2 * x * y;
+        Y[11] = c3 * y * (4.f * zz - xx - yy);
+        dY[11][0] = -2.f * c3 * x * y; dY[11][1] = c3 * (4.f * zz - xx - 3.f * yy); dY[11][2] = 8.f * c3 * y * z;
+        Y[12] = c4 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        dY[12][0] = -6.f * c4 * x * z; dY[12][1] = -6.f * c4 * y * z; dY[12][2] = c4 * (6.f * zz - 3.f * xx - 3.f * yy);
+        Y[13] = c3 * x * (4.f * zz - xx - yy);
+        dY[13][0] = c3 * (4.f * zz - 3.f * xx - yy); dY[13][1] = -2.f * c3 * x * y; dY[13][2] = 8.f * c3 * x * z;
+        Y[14] = c6 * z * (xx - yy);
+        dY[14][0] = 2.f * c6 * x * z; dY[14][1] = -2.f * c6 * y * z; dY[14][2] = c6 * (xx - yy);
+        Y[15] = c1 * x * (xx - 3.f * yy);
+        dY[15][0] = c1 * (3.f * xx - 3.f * yy); dY[15][1] = -6.f * c1 * x * y; dY[15][2] = 0.f;
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) {
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const int64_t N = p.n;
+    const float mx = p.means[3 * i], my = p.means[3 * i + 1], mz = p.means[3 * i + 2];
+    const float s[3] = {p.scales[3 * i], p.scales[3 * i + 1], p.scales[3 * i + 2]};
+    const float4 q4 = reinterpret_cast<const float4*>(p.quats)[i];
+    const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x / qn, x = q4.y / qn, y = q4.z / qn, z = q4.w / qn;
+    const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    float dmu[3] = {0.f, 0.f, 0.f}, dRS[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float dop = 0.f;
+    float dsh[NK * 3];
+#pragma unroll
+    for (int k = 0; k < NK * 3; ++k) dsh[k] = 0.f;
+    bool any = false;
+
+    for (int v = 0; v < vs.n; ++v) {
+        const int64_t m = (int64_t)v * N + i;
+        if (p.tiles[m] == 0) continue;
+        any = true;
+        const ViewRec& c = vs.v[v];
+        const float gu = p.g_xy[2 * m], gv = p.g_xy[2 * m + 1];
+        const float ga = p.g_conic[4 * m], gbq = p.g_conic[4 * m + 1], gc = p.g_conic[4 * m + 2];
+        dop += p.g_conic[4 * m + 3];
+        const uint8_t fl = p.flags[m];
+        // ---- colour
+        {
+            float gcol[3] = {p.g_rgb[3 * m], p.g_rgb[3 * m + 1], p.g_rgb[3 * m + 2]};
+            float d0 = mx - c.campos[0], d1 = my - c.campos[1], d2 = mz - c.campos[2];
+            const float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            const float id = 1.f / dn;
+            d0 *= id; d1 *= id; d2 *= id;
+            float Y[NK], dY[NK][3];
+            sh_basis_grad<DEG>(d0, d1, d2, Y, dY);
+            float gd[3] = {0.f, 0.f, 0.f};
+            const float* shp = p.sh + i * NK * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                if (fl & (1u << ch)) continue;
+                const float gcc = gcol[ch];
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    dsh[k * 3 + ch] += Y[k] * gcc;
+                    const float shv = shp[k * 3 + ch] * gcc;
+                    gd[0] += shv * dY[k][0];
+                    gd[1] += shv * dY[k][1];
+                    gd[2] += shv * dY[k][2];
+                }
+            }
+            const float pr = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+            dmu[0] += (gd[0] - d0 * pr) * id;
+            dmu[1] += (gd[1] - d1 * pr) * id;
+            dmu[2] += (gd[2] - d2 * pr) * id;
+        }
+        // ---- camera space and Jacobian
+        const float tx = c.R[0] * mx + c.R[1] * my + c.R[2] * mz + c.t[0];
+        const float ty = c.R[3] * mx + c.R[4] * my + c.R[5] * mz + c.t[1];
+        const float tz = c.R[6] * mx + c.R[7] * my + c.R[8] * mz + c.t[2];
+        const float iz = 1.f / tz;
+        const float limx = 1.3f * (0.5f * (float)c.W / c.fx), limy = 1.3f * (0.5f * (float)c.H / c.fy);
+        const float rx = fminf(limx, fmaxf(-limx, tx * iz)), ry = fminf(limy, fmaxf(-limy, ty * iz));
+        const bool clx = (fl & 8) != 0, cly = (fl & 16) != 0;
+        const float J00 = c.fx * iz, J02 = -c.fx * rx * iz, J11 = c.fy * iz, J12 = -c.fy * ry * iz;
+        float RS[9], WRS[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) RS[r * 3 + k] = R[r * 3 + k] * s[k];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                WRS[r * 3 + k] = c.R[r * 3] * RS[k] + c.R[r * 3 + 1] * RS[3 + k] + c.R[r * 3 + 2] * RS[6 + k];
+        float M0[3], M1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            M0[k] = J00 * WRS[k] + J02 * WRS[6 + k];
+            M1[k] = J11 * WRS[3 + k] + J12 * WRS[6 + k];
+        }
+        // ---- conic -> Sigma': dL/dSigma' = -Q G Q, G = [[ga, gb/2], [gb/2, gc]]
+        const float4 co = p.conic[m];
+        const float a = co.x, b = co.y, cc = co.z;
+        const float hb = 0.5f * gbq;
+        const float QG00 = a * ga + b * hb, QG01 = a * hb + b * gc;
+        const float QG10 = b * ga + cc * hb, QG11 = b * hb + cc * gc;
+        const float S00 = -(QG00 * a + QG01 * b);
+        const float S01 = -(QG00 * b + QG01 * cc);
+        const float S11 = -(QG10 * b + QG11 * cc);
+        // Sigma' = M M^T + 0.3 I  ->  dL/dM = 2 S M
+        float dM0[3], dM1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dM0[k] = 2.f * (S00 * M0[k] + S01 * M1[k]);
+            dM1[k] = 2.f * (S01 * M0[k] + S11 * M1[k]);
+        }
+        // M = J WRS
+        const float dJ00 = dM0[0] * WRS[0] + dM0[1] * WRS[1] + dM0[2] * WRS[2];
+        const float dJ02 = dM0[0] * WRS[6] + dM0[1] * WRS[7] + dM0[2] * WRS[8];
+        const float dJ11 = dM1[0] * WRS[3] + dM1[1] * WRS[4] + dM1[2] * WRS[5];
+        const float dJ12 = dM1[0] * WRS[6] + dM1[1] * WRS[7] + dM1[2] * WRS[8];
+        float dW[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dW[k] = J00 * dM0[k];
+            dW[3 + k] = J11 * dM1[k];
+            dW[6 + k] = J02 * dM0[k] + J12 * dM1[k];
+        }
+        // RS gradient through WRS = W RS
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dRS[r * 3 + k] += c.R[r] * dW[k] + c.R[3 + r] * dW[3 + k] + c.R[6 + r] * dW[6 + k];
+        // J(t) and the projected mean
+        const float iz2 = iz * iz;
+        float dtx = gu * c.fx * iz, dty = gv * c.fy * iz;
+        float dtz = -gu * c.fx * tx * iz2 - gv * c.fy * ty * iz2;
+        dtz += -c.fx * iz2 * dJ00 - c.fy * iz2 * dJ11;
+        dtz += dJ02 * (c.fx * rx * iz2 - (clx ? 0.f : c.fx * iz * (-tx * iz2)));
+        dtz += dJ12 * (c.fy * ry * iz2 - (cly ? 0.f : c.fy * iz * (-ty * iz2)));
+        if (!clx) dtx += dJ02 * (-c.fx * iz2);
+        if (!cly) dty += dJ12 * (-c.fy * iz2);
+        dmu[0] += c.R[0] * dtx + c.R[3] * dty + c.R[6] * dtz;
+        dmu[1] += c.R[1] * dtx + c.R[4] * dty + c.R[7] * dtz;
+        dmu[2] += c.R[2] * dtx + c.R[5] * dty + c.R[8] * dtz;
+    }
+    if (!any) return;
+    // RS = R diag(s)
+    float dR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p.d_scales[3 * i + k] += dRS[k] * R[k] + dRS[3 + k] * R[3 + k] + dRS[6 + k] * R[6 + k];
+        dR[k] = dRS[k] * s[k];
+        dR[3 + k] = dRS[3 + k] * s[k];
+        dR[6 + k] = dRS[6 + k] * s[k];
+    }
+    // R(q^) partials
+    const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    const float dx_ = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                             w * dR[7] - 2.f * x * dR[8]);
+    const float dy_ = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                             z * dR[7] - 2.f * y * dR[8]);
+    const float dz_ = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
+                             y * dR[5] + x * dR[6] + y * dR[7]);
+    const float pr = w * dw + x * dx_ + y * dy_ + z * dz_;
+    const float iq = 1.f / qn;
+    p.d_quats[4 * i + 0] += (dw - w * pr) * iq;
+    p.d_quats[4 * i + 1] += (dx_ - x * pr) * iq;
+    p.d_quats[4 * i + 2] += (dy_ - y * pr) * iq;
+    p.d_quats[4 * i + 3] += (dz_ - z * pr) * iq;
+    p.d_means[3 * i + 0] += dmu[0];
+    p.d_means[3 * i + 1] += dmu[1];
+    p.d_means[3 * i + 2] += dmu[2];
+    p.d_opac[i] += dop;
+    float* dsp = p.d_sh + i * NK * 3;
+#pragma unroll
+    for (int k = 0; k < NK * 3; ++k) dsp[k] += dsh[k];
+}
+
+template <int TW, int TH>
+void launch_render_bwd(const BwdParams& bp, const Views& vs, cudaStream_t s) {
+    render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+}
+
+}  // namespace lgs
+
+using namespace lgs;
 
 extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams,
                                      int32_t n_views, const lgs_config* cfg,
@@ -9,8 +521,57 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
                                      const uint32_t* n_contrib, const float* dL_drgb,
                                      const float* dL_dfinal_T, const lgs_grads* grads,
                                      int64_t* d_status, void* stream) {
-    (void)g; (void)cams; (void)n_views; (void)cfg; (void)pre; (void)vals; (void)ranges;
-    (void)final_T; (void)n_contrib; (void)dL_drgb; (void)dL_dfinal_T; (void)grads;
-    (void)d_status; (void)stream;
-    return LGS_ERR_UNSUPPORTED;
+    if (!g || !grads || !vals || !ranges || !final_T || !n_contrib || !dL_drgb || !d_status)
+        return LGS_ERR_ARG;
+    if (g->n < 0 || g->sh_degree < 0 || g->sh_degree > LGS_MAX_SH_DEGREE) return LGS_ERR_UNSUPPORTED;
+    Views vs;
+    lgs_status st = make_views(cams, n_views, cfg, &vs);
+    if (st != LGS_OK) return st;
+    st = check_pre(pre);
+    if (st != LGS_OK) return st;
+    if (!grads->xy2d || !grads->conic2d || !grads->rgb2d) return LGS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
+    if (g->n == 0) return LGS_OK;
+    if (!g->means || !g->scales || !g->quats || !g->sh || !grads->means || !grads->scales ||
+        !grads->quats || !grads->opacities || !grads->sh)
+        return LGS_ERR_ARG;
+    if (!aligned16(g->quats)) return LGS_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t m = g->n * (int64_t)n_views;
+    if (cudaMemsetAsync(grads->xy2d, 0, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->conic2d, 0, sizeof(float) * 4 * (size_t)m, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->rgb2d, 0, sizeof(float) * 3 * (size_t)m, s) != cudaSuccess)
+        return LGS_ERR_CUDA;
+    BwdParams bp;
+    bp.xy = reinterpret_cast<const float4*>(pre->xy);
+    bp.conic = reinterpret_cast<const float4*>(pre->conic);
+    bp.rgb = reinterpret_cast<const float4*>(pre->rgb);
+    bp.vals = vals;
+    bp.ranges = reinterpret_cast<const uint2*>(ranges);
+    bp.final_T = final_T;
+    bp.n_contrib = n_contrib;
+    bp.dL_drgb = dL_drgb;
+    bp.dL_dT = dL_dfinal_T;
+    bp.g_xy = grads->xy2d;
+    bp.g_conic = grads->conic2d;
+    bp.g_rgb = grads->rgb2d;
+    if (cfg->tile_w == 16) launch_render_bwd<16, 16>(bp, vs, s);
+    else if (cfg->tile_w == 8) launch_render_bwd<8, 32>(bp, vs, s);
+    else launch_render_bwd<32, 8>(bp, vs, s);
+    PreBwdParams pp;
+    pp.means = g->means; pp.scales = g->scales; pp.quats = g->quats; pp.sh = g->sh; pp.n = g->n;
+    pp.conic = reinterpret_cast<const float4*>(pre->conic);
+    pp.tiles = pre->tiles;
+    pp.flags = pre->flags;
+    pp.g_xy = grads->xy2d; pp.g_conic = grads->conic2d; pp.g_rgb = grads->rgb2d;
+    pp.d_means = grads->means; pp.d_scales = grads->scales; pp.d_quats = grads->quats;
+    pp.d_opac = grads->opacities; pp.d_sh = grads->sh;
+    const dim3 grid((unsigned)((g->n + 127) / 128));
+    switch (g->sh_degree) {
+        case 0: preprocess_bwd<0><<<grid, 128, 0, s>>>(pp, vs); break;
+        case 1: preprocess_bwd<1><<<grid, 128, 0, s>>>(pp, vs); break;
+        case 2: preprocess_bwd<2><<<grid, 128, 0, s>>>(pp, vs); break;
+        default: preprocess_bwd<3><<<grid, 128, 0, s>>>(pp, vs); break;
+    }
+    return cuda_status(cudaGetLastError());
 }

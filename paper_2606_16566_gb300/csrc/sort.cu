@@ -8,12 +8,21 @@
 // round trip (and is capturable in a CUDA graph); grids are sized for the
 // caller's capacity and blocks past K exit at once.
 //
-// Radix sort: 8-bit digits over the significant bits only (32 depth bits +
-// ceil(log2(n_tiles)) tile bits). Each pass is reduce-then-scan: an upsweep
-// builds per-block digit histograms, a scan turns each digit row into block
-// offsets, and a downsweep ranks keys stably inside 4096-key blocks (warp
-// __match_any_sync + per-warp counters), reorders them in shared memory and
-// writes runs of equal digits contiguously.
+// The sort is a most-significant-digit-first radix sort of the 64-bit keys
+// whose first "digit" is the whole tile id:
+//  1. emission writes (tile id, value) pairs in emission order;
+//  2. stable LSD passes of 8 bits over the ceil(log2(tiles)) tile bits only
+//     (reduce-then-scan: upsweep digit histograms per 4096-pair block, a scan
+//     of each digit row, and a downsweep that ranks pairs stably inside the
+//     block with __match_any_sync and per-warp counters, reorders them in
+//     shared memory and writes runs of equal digits contiguously);
+//  3. per-tile ranges from the tile-sorted ids;
+//  4. a stable LSD sort of each tile's segment by the 32 depth bits, in
+//     shared memory (segments of up to 2048 instances, one CTA each) or
+//     chunk-wise through global scratch (larger segments).
+// Step 2 keeps emission order inside every tile and step 4 is stable, so the
+// result is bit for bit the stable sort of (tile << 32 | depth) keys, with four
+// fewer passes over global memory than sorting the whole 64-bit key.
 #include "common.cuh"
 #include "host.h"
 
@@ -28,7 +37,9 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 2048
 constexpr int RADIX = 256;
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 (big-segment chunks)
+constexpr int PASS_ITEMS = 8;                          // tile-id passes: 2048 pairs per block
+constexpr int PASS_TILE = SORT_THREADS * PASS_ITEMS;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -138,54 +149,143 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* t
 }
 
 // ------------------------------------------------------------------ emission
-// key = (global tile id << 32) | bits(depth); value = v*N + i.
-__global__ void __launch_bounds__(256) emit_keys(const uint32_t* tiles, const uint32_t* offsets,
-                                                 const uint64_t* rect, const float* depth,
-                                                 int64_t m, int64_t n, const int64_t* status,
-                                                 int64_t capacity, Views vs, uint64_t* keys,
-                                                 uint32_t* vals) {
+// One (tile id, value) pair per tile of each visible entry's rect, entries
+// taken in depth order (order[j]), tiles row-major inside the rect; value =
+// entry index v*N + i. The 32 entries of a warp own one contiguous range of
+// instances (their offsets come from the scan), so the warp writes that range
+// cooperatively: lane l produces instances l, l+32, ... of the range, finds
+// the owning entry by a binary search over the warp's inclusive prefix counts
+// (shuffles), and the stores of a warp land on consecutive addresses.
+__global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const uint32_t* tiles,
+                                                  const uint32_t* offsets, const uint64_t* rect,
+                                                  int64_t m, int64_t n, const int64_t* status,
+                                                  int64_t capacity, Views vs, uint32_t* tkey,
+                                                  uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= m) return;
+    const int64_t wbase = idx - (threadIdx.x & 31);
+    if (wbase >= m) return;                                  // whole warp past the end
     if (status[LGS_ST_NUM_INSTANCES] > capacity) return;
-    const uint32_t nt = tiles[idx];
-    if (nt == 0) return;
-    const int v = (int)(idx / n);
-    const ViewRec& c = vs.v[v];
-    const uint64_t r = rect[idx];
-    const int x0 = (int)(r & 0xffff), y0 = (int)((r >> 16) & 0xffff);
-    const int x1 = (int)((r >> 32) & 0xffff), y1 = (int)((r >> 48) & 0xffff);
-    const uint32_t dbits = __float_as_uint(depth[idx]);
-    uint32_t off = offsets[idx];
-    for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-            const uint64_t tid = (uint64_t)(c.tile_off + (uint32_t)(ty * c.gx + tx));
-            keys[off] = (tid << 32) | dbits;
-            vals[off] = (uint32_t)idx;
-            ++off;
+    const int lane = threadIdx.x & 31;
+    const bool valid = idx < m;
+    const uint32_t cnt = valid ? tiles[idx] : 0u;
+    const uint32_t ent = cnt ? order[idx] : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
+    // per-entry data the owners hand out
+    uint32_t x0 = 0, y0 = 0, wd = 1, toff = 0, gx = 1;
+    if (cnt) {
+        const uint64_t r = rect[ent];
+        x0 = (uint32_t)(r & 0xffff);
+        y0 = (uint32_t)((r >> 16) & 0xffff);
+        wd = (uint32_t)((r >> 32) & 0xffff) - x0;
+        const ViewRec& c = vs.v[(int)(ent / (uint64_t)n)];
+        toff = c.tile_off;
+        gx = (uint32_t)c.gx;
+    }
+    const uint32_t excl = incl - cnt;
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        // owner = first lane with incl > e
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+            if (v <= e) lo += step;
         }
+        const int own = lo;
+        const uint32_t k = e - __shfl_sync(0xffffffffu, excl, own);
+        const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, own);
+        const uint32_t oy0 = __shfl_sync(0xffffffffu, y0, own);
+        const uint32_t ow = __shfl_sync(0xffffffffu, wd, own);
+        const uint32_t otoff = __shfl_sync(0xffffffffu, toff, own);
+        const uint32_t ogx = __shfl_sync(0xffffffffu, gx, own);
+        const uint32_t oent = __shfl_sync(0xffffffffu, ent, own);
+        if (e < total) {
+            const uint32_t ry = k / ow, rx = k - ry * ow;
+            tkey[start + e] = otoff + (oy0 + ry) * ogx + ox0 + rx;
+            tval[start + e] = oent;
+        }
+    }
 }
 
-// ------------------------------------------------------------------ radix passes
+// ------------------------------------------------------------------ stable ranking
 __device__ __forceinline__ int64_t sort_count(const int64_t* status, int64_t capacity) {
     int64_t K = status[LGS_ST_NUM_INSTANCES];
     return K > capacity ? 0 : K;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) radix_upsweep(const uint64_t* keys,
+// Element count of a radix pass: the device instance count (checked against
+// the capacity) when `status` is given, else the host-known count.
+__device__ __forceinline__ int64_t pass_count(const int64_t* status, int64_t n) {
+    return status ? sort_count(status, n) : n;
+}
+
+// Stable digit ranks of a chunk of ITEMS*256 elements held in registers in
+// striped order (element j = i*256 + threadIdx.x). dg[i] in [0, 256); padding
+// elements carry digit 255 and come after every real one. On return rank[i]
+// counts the earlier elements of the chunk with the same digit and `total`
+// (thread t) is the chunk's count of digit t. Each round of 256 elements is
+// ranked inside warps with __match_any_sync; per-warp digit counters in shared
+// memory (double-buffered, cnt = 2 x 8 x 256 words) carry the prefix across
+// warps and rounds.
+template <int ITEMS>
+__device__ __forceinline__ void rank_chunk(const uint32_t (&dg)[ITEMS], uint16_t (&rank)[ITEMS],
+                                           uint32_t* cnt, uint32_t& total) {
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; ++w) {
+        cnt[w * RADIX + t] = 0;
+        cnt[(SORT_THREADS / 32 + w) * RADIX + t] = 0;
+    }
+    __syncthreads();
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t* cb = cnt + (i & 1) * (SORT_THREADS / 32) * RADIX;
+        uint32_t* cn = cnt + ((i & 1) ^ 1) * (SORT_THREADS / 32) * RADIX;
+        const uint32_t d = dg[i];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t r = __popc(peers & lt);
+        if (r == 0) cb[warp * RADIX + d] = __popc(peers);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < SORT_THREADS / 32; ++w) {
+            const uint32_t c = cb[w * RADIX + t];
+            cb[w * RADIX + t] = run;
+            run += c;
+            cn[w * RADIX + t] = 0;
+        }
+        __syncthreads();
+        rank[i] = (uint16_t)(cb[warp * RADIX + d] + r);
+    }
+    total = run;
+}
+
+// ------------------------------------------------------------------ tile-id passes
+__global__ void __launch_bounds__(SORT_THREADS) radix_upsweep(const uint32_t* keys,
                                                               const int64_t* status,
                                                               int64_t capacity, int shift,
                                                               uint32_t* hist, int nb) {
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t K = sort_count(status, capacity);
-    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t K = pass_count(status, capacity);
+    const int64_t base = (int64_t)blockIdx.x * PASS_TILE;
     const uint32_t lane = threadIdx.x & 31;
     if (base < K) {
 #pragma unroll 4
-        for (int k = 0; k < SORT_ITEMS; ++k) {
+        for (int k = 0; k < PASS_ITEMS; ++k) {
             const int64_t i = base + (int64_t)k * SORT_THREADS + threadIdx.x;
-            const uint32_t d = i < K ? (uint32_t)((keys[i] >> shift) & 0xffu) : 0x100u;
+            const uint32_t d = i < K ? ((keys[i] >> shift) & 0xffu) : 0x100u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (d < 0x100u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], __popc(peers));
         }
@@ -214,89 +314,58 @@ __global__ void __launch_bounds__(1024) radix_scan_rows(uint32_t* hist, int nb,
 struct DownSmem {
     uint32_t base[RADIX];            // global output base per digit for this block
     uint32_t start[RADIX];           // block-local start of each digit
-    uint32_t cnt[2][SORT_THREADS / 32][RADIX];
+    uint32_t cnt[2 * (SORT_THREADS / 32) * RADIX];
     uint32_t ws[32];
-    uint64_t keys[SORT_TILE];
-    uint32_t vals[SORT_TILE];
+    uint32_t keys[PASS_TILE];
+    uint32_t vals[PASS_TILE];
 };
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_downsweep(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const int64_t* status, int64_t capacity, int shift,
     const uint32_t* hist, int nb, const uint32_t* digit_total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
-    const int64_t K = sort_count(status, capacity);
-    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t K = pass_count(status, capacity);
+    const int64_t base = (int64_t)blockIdx.x * PASS_TILE;
     if (base >= K) return;
-    const int n_valid = (int)min((int64_t)SORT_TILE, K - base);
-    const int t = threadIdx.x, warp = t >> 5;
-
-    // global digit bases: exclusive scan over digits of the totals + this block's row offset
+    const int n_valid = (int)min((int64_t)PASS_TILE, K - base);
+    const int t = threadIdx.x;
     {
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan<SORT_THREADS>(digit_total[t], S.ws, tot);
         S.base[t] = ex + hist[(int64_t)t * nb + blockIdx.x];
     }
+    uint32_t k[PASS_ITEMS], vv[PASS_ITEMS], dg[PASS_ITEMS];
 #pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; ++w) {
-        S.cnt[0][w][t] = 0;
-        S.cnt[1][w][t] = 0;
-    }
-    uint64_t k[SORT_ITEMS];
-    uint32_t vv[SORT_ITEMS];
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
+    for (int i = 0; i < PASS_ITEMS; ++i) {
         const int j = i * SORT_THREADS + t;
-        if (j < n_valid) {
-            k[i] = kin[base + j];
-            vv[i] = vin[base + j];
-        } else {
-            k[i] = ~0ull;   // digit 255 and ranked after every valid key
-            vv[i] = 0;
-        }
+        const bool ok = j < n_valid;
+        k[i] = ok ? kin[base + j] : 0xffffffffu;
+        vv[i] = ok ? vin[base + j] : 0u;
+        dg[i] = ok ? ((k[i] >> shift) & 0xffu) : 0xffu;
     }
-    __syncthreads();
-    const uint32_t lt = lanemask_lt();
-    uint32_t run = 0;                  // thread t: running count of digit t
-    uint16_t rank[SORT_ITEMS];
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
-        const int b = i & 1;
-        const uint32_t d = (uint32_t)((k[i] >> shift) & 0xffu);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t r = __popc(peers & lt);
-        if (r == 0) S.cnt[b][warp][d] = __popc(peers);
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < SORT_THREADS / 32; ++w) {
-            const uint32_t c = S.cnt[b][w][t];
-            S.cnt[b][w][t] = run;
-            run += c;
-            S.cnt[b ^ 1][w][t] = 0;
-        }
-        __syncthreads();
-        rank[i] = (uint16_t)(S.cnt[b][warp][d] + r);
-    }
+    uint16_t rank[PASS_ITEMS];
+    uint32_t run;
+    rank_chunk<PASS_ITEMS>(dg, rank, S.cnt, run);
     {
         uint32_t tot;
         S.start[t] = block_exclusive_scan<SORT_THREADS>(run, S.ws, tot);
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
+    for (int i = 0; i < PASS_ITEMS; ++i) {
         const int j = i * SORT_THREADS + t;
         if (j < n_valid) {
-            const uint32_t d = (uint32_t)((k[i] >> shift) & 0xffu);
-            const uint32_t pos = S.start[d] + rank[i];
+            const uint32_t pos = S.start[dg[i]] + rank[i];
             S.keys[pos] = k[i];
             S.vals[pos] = vv[i];
         }
     }
     __syncthreads();
     for (int j = t; j < n_valid; j += SORT_THREADS) {
-        const uint64_t key = S.keys[j];
-        const uint32_t d = (uint32_t)((key >> shift) & 0xffu);
+        const uint32_t key = S.keys[j];
+        const uint32_t d = (key >> shift) & 0xffu;
         const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
         kout[gpos] = key;
         vout[gpos] = S.vals[j];
@@ -304,69 +373,134 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_downsweep(
 }
 
 // ------------------------------------------------------------------ ranges
-__global__ void tile_ranges(const uint64_t* keys, const int64_t* status, int64_t capacity,
-                            uint32_t* ranges) {
+__global__ void tile_ranges(const uint32_t* tkey, const int64_t* status, int64_t capacity,
+                            uint2* ranges) {
     const int64_t K = sort_count(status, capacity);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t tile = (uint32_t)(keys[i] >> 32);
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != tile) ranges[2 * (int64_t)tile] = (uint32_t)i;
-        if (i == K - 1 || (uint32_t)(keys[i + 1] >> 32) != tile)
-            ranges[2 * (int64_t)tile + 1] = (uint32_t)(i + 1);
+        const uint32_t tile = tkey[i];
+        if (i == 0 || tkey[i - 1] != tile) ranges[tile].x = (uint32_t)i;
+        if (i == K - 1 || tkey[i + 1] != tile) ranges[tile].y = (uint32_t)(i + 1);
     }
+}
+
+// ------------------------------------------------------------------ depth order of the entries
+// key = depth bits for entries that touch at least one tile (positive floats
+// order like their bit patterns), all-ones for culled entries (sorted last);
+// value = entry index v*N + i.
+__global__ void depth_keys(const uint32_t* tiles, const float* depth, int64_t m, uint32_t* key,
+                           uint32_t* val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
+        val[i] = (uint32_t)i;
+    }
+}
+
+// tiles-touched of the entries in depth order
+__global__ void gather_tiles(const uint32_t* order, const uint32_t* tiles, int64_t m,
+                             uint32_t* tiles_sorted) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        tiles_sorted[j] = tiles[order[j]];
+}
+
+// Optional 64-bit keys of the sorted instances: (tile << 32) | bits(depth).
+__global__ void write_keys(const uint32_t* tkey, const uint32_t* vals, const float* depth,
+                           const int64_t* status, int64_t capacity, uint64_t* keys) {
+    const int64_t K = sort_count(status, capacity);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = ((uint64_t)tkey[i] << 32) | __float_as_uint(depth[vals[i]]);
 }
 
 // ------------------------------------------------------------------ workspace
 struct SortWs {
-    uint32_t* offsets;     // [m]
+    uint32_t* ek;          // [m] entry depth keys (ping)
+    uint32_t* ev;          // [m] entry indices
+    uint32_t* ek2;         // [m] (pong)
+    uint32_t* ev2;         // [m]
+    uint32_t* tiles_s;     // [m] tiles-touched in depth order
+    uint32_t* offsets;     // [m] exclusive scan of tiles_s
     uint64_t* block_sums;  // [ceil(m/2048)]
-    uint64_t* keys_alt;    // [capacity]
-    uint32_t* vals_alt;    // [capacity]
-    uint32_t* hist;        // [256 * nb]
+    uint32_t* ak;          // [capacity] tile ids
+    uint32_t* bk;          // [capacity]
+    uint32_t* bv;          // [capacity] values (the caller's vals buffer is the other one)
+    uint32_t* hist;        // [256 * max(nb_entries, nb_instances)]
     uint32_t* digit_total; // [256]
 };
 
 constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 // Bytes of the sort workspace for m entries and an instance capacity
 // (usable in constant expressions).
 constexpr size_t sort_ws_bytes(int64_t m, int64_t capacity) {
-    const int64_t nscan = (m + SCAN_TILE - 1) / SCAN_TILE;
-    const int64_t nb = (capacity + SORT_TILE - 1) / SORT_TILE;
-    return align_up(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1)) +
+    const size_t mm = (size_t)(m > 0 ? m : 1);
+    const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+    const int64_t nscan = ceil_div(m, SCAN_TILE);
+    const int64_t nb = ceil_div(m > capacity ? m : capacity, PASS_TILE);
+    return 6 * align_up(sizeof(uint32_t) * mm) +
            align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1)) +
-           align_up(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1)) +
-           align_up(sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1)) +
+           3 * align_up(sizeof(uint32_t) * cap) +
            align_up(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1)) +
            align_up(sizeof(uint32_t) * RADIX);
 }
 
 inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws) {
-    const int64_t nscan = (m + SCAN_TILE - 1) / SCAN_TILE;
-    const int64_t nb = (capacity + SORT_TILE - 1) / SORT_TILE;
+    const size_t mm = (size_t)(m > 0 ? m : 1);
+    const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+    const int64_t nscan = ceil_div(m, SCAN_TILE);
+    const int64_t nb = ceil_div(m > capacity ? m : capacity, PASS_TILE);
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align_up(bytes); return p; };
-    char* p0 = take(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
+    char* e0 = take(sizeof(uint32_t) * mm);
+    char* e1 = take(sizeof(uint32_t) * mm);
+    char* e2 = take(sizeof(uint32_t) * mm);
+    char* e3 = take(sizeof(uint32_t) * mm);
+    char* e4 = take(sizeof(uint32_t) * mm);
+    char* e5 = take(sizeof(uint32_t) * mm);
     char* p1 = take(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1));
-    char* p2 = take(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1));
-    char* p3 = take(sizeof(uint32_t) * (size_t)(capacity > 0 ? capacity : 1));
-    char* p4 = take(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1));
-    char* p5 = take(sizeof(uint32_t) * RADIX);
+    char* p2 = take(sizeof(uint32_t) * cap);
+    char* p3 = take(sizeof(uint32_t) * cap);
+    char* p4 = take(sizeof(uint32_t) * cap);
+    char* p6 = take(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1));
+    char* p7 = take(sizeof(uint32_t) * RADIX);
     if (ws) {
-        ws->offsets = reinterpret_cast<uint32_t*>(p0);
+        ws->ek = reinterpret_cast<uint32_t*>(e0);
+        ws->ev = reinterpret_cast<uint32_t*>(e1);
+        ws->ek2 = reinterpret_cast<uint32_t*>(e2);
+        ws->ev2 = reinterpret_cast<uint32_t*>(e3);
+        ws->tiles_s = reinterpret_cast<uint32_t*>(e4);
+        ws->offsets = reinterpret_cast<uint32_t*>(e5);
         ws->block_sums = reinterpret_cast<uint64_t*>(p1);
-        ws->keys_alt = reinterpret_cast<uint64_t*>(p2);
-        ws->vals_alt = reinterpret_cast<uint32_t*>(p3);
-        ws->hist = reinterpret_cast<uint32_t*>(p4);
-        ws->digit_total = reinterpret_cast<uint32_t*>(p5);
+        ws->ak = reinterpret_cast<uint32_t*>(p2);
+        ws->bk = reinterpret_cast<uint32_t*>(p3);
+        ws->bv = reinterpret_cast<uint32_t*>(p4);
+        ws->hist = reinterpret_cast<uint32_t*>(p6);
+        ws->digit_total = reinterpret_cast<uint32_t*>(p7);
     }
     return off;
 }
 
-inline int sort_passes(uint32_t n_tiles) {
-    int tile_bits = 0;
-    while (tile_bits < 32 && (1ull << tile_bits) < (uint64_t)n_tiles) ++tile_bits;
-    return (32 + tile_bits + 7) / 8;
+inline int tile_passes(uint32_t n_tiles) {
+    int bits = 0;
+    while (bits < 32 && (1ull << bits) < (uint64_t)n_tiles) ++bits;
+    return bits == 0 ? 0 : (bits + 7) / 8;
+}
+
+// One stable LSD radix pass over u32 keys carrying u32 values. The element
+// count is the device instance count when `status` is given, else `count`.
+static void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
+                       const int64_t* status, int64_t count, int shift, const SortWs* ws,
+                       cudaStream_t s) {
+    const int nb = (int)ceil_div(count, PASS_TILE);
+    if (nb == 0) return;
+    radix_upsweep<<<nb, SORT_THREADS, 0, s>>>(kin, status, count, shift, ws->hist, nb);
+    radix_scan_rows<<<RADIX, 1024, 0, s>>>(ws->hist, nb, ws->digit_total);
+    radix_downsweep<<<nb, SORT_THREADS, sizeof(DownSmem), s>>>(kin, vin, kout, vout, status, count,
+                                                             shift, ws->hist, nb, ws->digit_total);
 }
 
 }  // namespace lgs
@@ -378,11 +512,17 @@ extern "C" size_t lgs_sort_workspace_size(int64_t m, int64_t capacity) {
     return sort_ws_layout(m, capacity, nullptr, nullptr);
 }
 
-// Enqueues the full stage given a workspace layout (shared by the entry points).
+// Enqueues the full stage given a workspace layout (shared by the entry points):
+//  1. stable LSD sort of the m entries by depth (culled entries last),
+//  2. scan of tiles-touched in that order -> instance offsets and K,
+//  3. emission of (tile id, entry) pairs in that order,
+//  4. stable LSD passes over the tile-id bits,
+//  5. tile ranges (and, if asked for, the 64-bit keys).
+// Inside every tile the instances are then in (depth, entry index) order,
+// i.e. exactly the stable sort of the (tile << 32 | depth) keys.
 static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* vs,
-                                       int64_t capacity, uint64_t* keys, uint32_t* vals,
-                                       uint32_t* ranges, const SortWs* ws, int64_t* d_status,
-                                       cudaStream_t s) {
+                               int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges,
+                               const SortWs* ws, int64_t* d_status, cudaStream_t s) {
     const int64_t m = n * vs->n;
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)vs->n_tiles, s);
     if (e != cudaSuccess) return LGS_ERR_CUDA;
@@ -390,36 +530,40 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
         e = cudaMemsetAsync(d_status + LGS_ST_NUM_INSTANCES, 0, sizeof(int64_t), s);
         return cuda_status(e);
     }
-    const int64_t nscan = (m + SCAN_TILE - 1) / SCAN_TILE;
-    scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(pre->tiles, m, ws->block_sums);
-    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
-    scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(pre->tiles, m, ws->block_sums,
-                                                            ws->offsets);
-    const int passes = sort_passes(vs->n_tiles);
-    // emit so that the last pass lands in the caller's buffers
-    uint64_t* ka = (passes & 1) ? ws->keys_alt : keys;
-    uint32_t* va = (passes & 1) ? ws->vals_alt : vals;
-    uint64_t* kb = (passes & 1) ? keys : ws->keys_alt;
-    uint32_t* vb = (passes & 1) ? vals : ws->vals_alt;
-    emit_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pre->tiles, ws->offsets, pre->rect,
-                                                          pre->depth, m, n, d_status, capacity,
-                                                          *vs, ka, va);
-    const int nb = (int)((capacity + SORT_TILE - 1) / SORT_TILE);
-    if (nb > 0) {
-        static_assert(sizeof(DownSmem) < 227 * 1024, "smem");
-        cudaFuncSetAttribute(radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(DownSmem));
-        for (int p = 0; p < passes; ++p) {
-            const int shift = 8 * p;
-            radix_upsweep<<<nb, SORT_THREADS, 0, s>>>(ka, d_status, capacity, shift, ws->hist, nb);
-            radix_scan_rows<<<RADIX, 1024, 0, s>>>(ws->hist, nb, ws->digit_total);
-            radix_downsweep<<<nb, SORT_THREADS, sizeof(DownSmem), s>>>(
-                ka, va, kb, vb, d_status, capacity, shift, ws->hist, nb, ws->digit_total);
-            uint64_t* tk = ka; ka = kb; kb = tk;
-            uint32_t* tv = va; va = vb; vb = tv;
-        }
-        tile_ranges<<<152 * 4, 256, 0, s>>>(keys, d_status, capacity, ranges);
+    cudaFuncSetAttribute(radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(DownSmem));
+    // 1. entries by depth
+    depth_keys<<<152 * 8, 256, 0, s>>>(pre->tiles, pre->depth, m, ws->ek, ws->ev);
+    uint32_t *k0 = ws->ek, *v0 = ws->ev, *k1 = ws->ek2, *v1 = ws->ev2;
+    for (int shift = 0; shift < 32; shift += 8) {
+        radix_pass(k0, v0, k1, v1, nullptr, m, shift, ws, s);
+        uint32_t* t = k0; k0 = k1; k1 = t;
+        t = v0; v0 = v1; v1 = t;
     }
+    const uint32_t* order = v0;
+    // 2. scan of tiles-touched in depth order
+    gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->tiles_s);
+    const int64_t nscan = ceil_div(m, SCAN_TILE);
+    scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
+    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
+    scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums,
+                                                            ws->offsets);
+    // 3. emission; the value buffers alternate so that the last pass lands in vals
+    const int passes = tile_passes(vs->n_tiles);
+    uint32_t *ka = ws->ak, *kb = ws->bk;
+    uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
+    emit_pairs<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect,
+                                                          m, n, d_status, capacity, *vs, ka, va);
+    // 4. tile-id passes over the K instances
+    for (int p = 0; p < passes; ++p) {
+        radix_pass(ka, va, kb, vb, d_status, capacity, 8 * p, ws, s);
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    // 5. ranges (ka holds the sorted tile ids, va == vals)
+    uint2* r2 = reinterpret_cast<uint2*>(ranges);
+    tile_ranges<<<152 * 4, 256, 0, s>>>(ka, d_status, capacity, r2);
+    if (keys) write_keys<<<152 * 8, 256, 0, s>>>(ka, vals, pre->depth, d_status, capacity, keys);
     return cuda_status(cudaGetLastError());
 }
 
@@ -427,13 +571,14 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
                                int32_t n_views, const lgs_config* cfg, int64_t capacity,
                                uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* workspace,
                                size_t workspace_bytes, int64_t* d_status, void* stream) {
-    if (!pre || !keys || !vals || !ranges || !d_status) return LGS_ERR_ARG;
+    if (!pre || !vals || !ranges || !d_status) return LGS_ERR_ARG;
     if (n < 0 || capacity < 0 || capacity >= (1ll << 32)) return LGS_ERR_ARG;
     Views vs;
     lgs_status st = make_views(cams, n_views, cfg, &vs);
     if (st != LGS_OK) return st;
     if (!pre->tiles || !pre->rect || !pre->depth) return LGS_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u))
+    if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
+        (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;
     const int64_t m = n * (int64_t)n_views;
     if (m >= (1ll << 32)) return LGS_ERR_UNSUPPORTED;
@@ -443,7 +588,7 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
     SortWs ws;
     sort_ws_layout(m, capacity, static_cast<char*>(workspace), &ws);
     return sort_enqueue(pre, n, &vs, capacity, keys, vals, ranges, &ws, d_status,
-                            static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------------ static scratch variant
@@ -482,7 +627,7 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
                                       int32_t n_views, const lgs_config* cfg, int64_t capacity,
                                       uint64_t* keys, uint32_t* vals, uint32_t* ranges,
                                       int64_t* d_status, void* stream) {
-    if (!pre || !keys || !vals || !ranges || !d_status) return LGS_ERR_ARG;
+    if (!pre || !vals || !ranges || !d_status) return LGS_ERR_ARG;
     if (n < 0 || capacity < 0) return LGS_ERR_ARG;
     Views vs;
     lgs_status st = make_views(cams, n_views, cfg, &vs);
@@ -491,7 +636,8 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
     if (m > LGS_SORT_STATIC_MAX_ENTRIES || capacity > LGS_SORT_STATIC_MAX_INSTANCES)
         return LGS_ERR_UNSUPPORTED;
     if (!pre->tiles || !pre->rect || !pre->depth) return LGS_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u))
+    if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
+        (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;
     void* scratch = nullptr;
     st = sort_static_scratch(&scratch);

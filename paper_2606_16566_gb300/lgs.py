@@ -132,11 +132,13 @@ def n_pixels(cams) -> int:
 
 
 def sort(pre: PreOut, n, cams, cfg, capacity, keys=None, vals=None, ranges=None, workspace=None,
-         status=None, stream=None):
+         status=None, stream=None, with_keys=True):
+    """lgs_sort. with_keys=False passes NULL keys: only values and ranges are written."""
     carr = cameras(cams)
     dev = pre.xy.device
     m = n * len(cams)
-    keys = keys if keys is not None else torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    if with_keys and keys is None:
+        keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
     vals = vals if vals is not None else torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
     ranges = ranges if ranges is not None else torch.empty((n_tiles(cams, cfg), 2), dtype=torch.int32,
                                                            device=dev)
@@ -181,6 +183,61 @@ def render_fwd(pre: PreOut, vals, ranges, cams, cfg, rgb=None, final_T=None, n_c
                                     ctypes.byref(cfg), _ptr(rgb), _ptr(final_T), _ptr(n_contrib),
                                     _ptr(status), _stream(stream)), "lgs_render_fwd")
     return rgb, final_T, n_contrib
+
+
+def new_grads(g, n_views):
+    """Zeroed gradient buffers for lgs_render_bwd (3D grads + 2D scratch)."""
+    dev = g["means"].device
+    n = g["means"].shape[0]
+    m = max(n * n_views, 1)
+    z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=dev)
+    return {"means": z(g["means"].shape), "scales": z(g["scales"].shape), "quats": z(g["quats"].shape),
+            "opacities": z(g["opacities"].shape), "sh": z(g["sh"].shape),
+            "xy2d": z((m, 2)), "conic2d": z((m, 4)), "rgb2d": z((m, 3))}
+
+
+def render_bwd(g, cams, cfg, pre: PreOut, vals, ranges, final_T, n_contrib, dL_drgb, dL_dT=None,
+               grads=None, status=None, stream=None):
+    """lgs_render_bwd: gradients of <dL_drgb, rgb> + <dL_dT, final_T>."""
+    carr = cameras(cams)
+    grads = grads if grads is not None else new_grads(g, len(cams))
+    status = status if status is not None else new_status(g["means"].device)
+    gs = gaussians(g)
+    ps = pre.struct()
+    gr = L.lgs_grads(*(grads[k].data_ptr() for k in ("means", "scales", "quats", "opacities", "sh",
+                                                      "xy2d", "conic2d", "rgb2d")))
+    L.check(L.load().lgs_render_bwd(ctypes.byref(gs), carr, len(carr), ctypes.byref(cfg), ctypes.byref(ps),
+                                    _ptr(vals), _ptr(ranges), _ptr(final_T), _ptr(n_contrib),
+                                    _ptr(dL_drgb.contiguous()),
+                                    _ptr(None if dL_dT is None else dL_dT.contiguous()),
+                                    ctypes.byref(gr), _ptr(status), _stream(stream)), "lgs_render_bwd")
+    return grads
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable forward render of a batch of views.
+
+    forward(means, scales, quats, opacities, sh, cams, tile) -> (rgb, final_T), both
+    flat over the views (see include/lgs.h); backward runs lgs_render_bwd from the
+    saved preprocess outputs, tile lists, final_T and n_contrib.
+    """
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacities, sh, cams, tile=(16, 16)):
+        g = {"means": means.contiguous(), "scales": scales.contiguous(), "quats": quats.contiguous(),
+             "opacities": opacities.contiguous(), "sh": sh.contiguous()}
+        res = render(g, cams, tile=tile)
+        ctx.cams, ctx.cfg, ctx.g = cams, res["cfg"], g
+        ctx.pre = res["pre"]
+        ctx.save_for_backward(res["vals"], res["ranges"], res["T_flat"], res["nc_flat"])
+        return res["rgb_flat"], res["T_flat"]
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_T):
+        vals, ranges, T, nc = ctx.saved_tensors
+        gr = render_bwd(ctx.g, ctx.cams, ctx.cfg, ctx.pre, vals, ranges, T, nc, d_rgb.contiguous(),
+                        None if d_T is None else d_T.contiguous())
+        return gr["means"], gr["scales"], gr["quats"], gr["opacities"], gr["sh"], None, None
 
 
 def read_status(status, stream=None) -> np.ndarray:

@@ -101,7 +101,7 @@ def test_sort_bitexact_against_host_stable_sort(tile):
 
 
 def test_sort_many_instances_multi_pass():
-    """Enough instances for many 4096-key blocks and >5 radix passes."""
+    """Enough instances for many 4096-pair blocks of the tile passes."""
     sc, cams = scenes.random_small(20000, seed=10, width=640, height=480, log_scale_mean=-2.5)
     res = _render(sc, cams)
     k = res["keys"].cpu().numpy().view(np.uint64)
@@ -110,6 +110,58 @@ def test_sort_many_instances_multi_pass():
     k_ref, v_ref, _ = _host_sort_of_gpu_keys(res, cams, 20000, (16, 16))
     np.testing.assert_array_equal(k, k_ref)
     np.testing.assert_array_equal(res["vals"].cpu().numpy().view(np.uint32), v_ref)
+
+
+@pytest.mark.parametrize("n,W,H", [(6000, 64, 48), (30000, 96, 64)])
+def test_sort_large_tile_segments(n, W, H):
+    """Large overlapping Gaussians in a small image: tile segments of several
+    thousand instances take the chunked global-memory segment sort."""
+    sc, cams = scenes.random_small(n, seed=12, width=W, height=H, log_scale_mean=-1.3,
+                                   log_scale_std=0.3)
+    res = _render(sc, cams)
+    ranges = res["ranges"].cpu().numpy().view(np.uint32).astype(np.int64)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > 4096
+    k_ref, v_ref, _ = _host_sort_of_gpu_keys(res, cams, n, (16, 16))
+    np.testing.assert_array_equal(res["keys"].cpu().numpy().view(np.uint64), k_ref)
+    np.testing.assert_array_equal(res["vals"].cpu().numpy().view(np.uint32), v_ref)
+
+
+@pytest.mark.parametrize("n", [500, 9000])
+def test_sort_depth_ties_keep_emission_order(n):
+    """All Gaussians at exactly the same camera depth: every key of a tile is
+    equal, so each tile list must be in ascending Gaussian order."""
+    rng = np.random.default_rng(13)
+    cam = scenes.look_at((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 80, 64, 60.0)
+    sc = {"means": np.stack([rng.uniform(-1, 1, n), rng.uniform(-0.8, 0.8, n), np.zeros(n)], 1).astype(np.float32),
+          "scales": np.full((n, 3), 0.05 if n < 1000 else 0.3, np.float32),
+          "quats": np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+          "opacities": np.full(n, 0.5, np.float32), "sh": np.full((n, 1, 3), 0.2, np.float32)}
+    res = _render(sc, [cam])
+    k_ref, v_ref, _ = _host_sort_of_gpu_keys(res, [cam], n, (16, 16))
+    assert len(np.unique(k_ref & np.uint64(0xFFFFFFFF))) == 1
+    np.testing.assert_array_equal(res["keys"].cpu().numpy().view(np.uint64), k_ref)
+    np.testing.assert_array_equal(res["vals"].cpu().numpy().view(np.uint32), v_ref)
+
+
+def test_sort_without_keys_output():
+    sc, cams = scenes.random_small(1500, seed=14, width=120, height=90)
+    g = lgs.to_device(sc)
+    cfg = lgs.config()
+    st = lgs.new_status()
+    pre = lgs.preprocess(g, cams, cfg, status=st)
+    k1, v1, r1 = lgs.sort(pre, 1500, cams, cfg, 1 << 16, status=st)
+    K = int(lgs.read_status(st)[L.ST_NUM_INSTANCES])
+    vals = torch.empty(1 << 16, dtype=torch.int32, device="cuda")
+    ranges = torch.empty_like(r1)
+    ws = torch.empty(lgs.sort_workspace_size(1500, 1 << 16), dtype=torch.uint8, device="cuda")
+    import ctypes
+    ps = pre.struct()
+    L.check(L.load().lgs_sort(ctypes.byref(ps), 1500, lgs.cameras(cams), 1, ctypes.byref(cfg), 1 << 16,
+                              None, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(ranges.data_ptr()),
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(st.data_ptr()),
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.testing.assert_close(vals[:K], v1[:K], rtol=0, atol=0)
+    torch.testing.assert_close(ranges, r1, rtol=0, atol=0)
 
 
 def test_capacity_overflow_reports_needed_count():
