@@ -190,6 +190,21 @@ class Pipeline:
         self.stage_sort(cfg)
         self.stage_render(cfg)
 
+    def setup_backward(self, seed=0):
+        """Gradient buffers and a fixed upstream gradient dL/drgb (the shape of an
+        L1 loss gradient: +-1/numel), so the backward step runs only our kernels."""
+        torch = self.torch
+        gen = torch.Generator(device=self.rgb.device).manual_seed(seed)
+        sign = torch.randint(0, 2, self.rgb.shape, generator=gen, device=self.rgb.device)
+        self.d_rgb = (sign.float() * 2 - 1) / self.rgb.numel()
+        self.grads = self.lgs.new_grads(self.g, len(self.cams))
+
+    def stage_backward(self, cfg):
+        for k in ("means", "scales", "quats", "opacities", "sh"):
+            self.grads[k].zero_()
+        self.lgs.render_bwd(self.g, self.cams, cfg, self.pre, self.vals, self.ranges, self.T, self.nc,
+                            self.d_rgb, None, self.grads, self.status)
+
     def launches(self):
         """Kernels of one step: preprocess; depth keys + 4 entry passes (3 kernels
         each); gather + 3 scan kernels; emission; tile-id passes; ranges; render."""
@@ -202,9 +217,10 @@ class Pipeline:
         return 1 + 1 + 4 * 3 + 1 + 3 + 1 + 3 * tile_passes + 1 + 1
 
 
-def time_steps(pipe, cfg, steps, flush):
+def time_steps(pipe, cfg, steps, flush, backward=False):
     import torch
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    ns = 4 if backward else 3
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
         e = ev[i]
@@ -215,9 +231,12 @@ def time_steps(pipe, cfg, steps, flush):
         e[2].record()
         pipe.stage_render(cfg)
         e[3].record()
+        if backward:
+            pipe.stage_backward(cfg)
+            e[4].record()
     torch.cuda.synchronize()
-    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in ev])
-    return stage  # [steps, 3] ms
+    stage = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(ns)] for e in ev])
+    return stage  # [steps, stages] ms
 
 
 def run_ours(args, rank, world):
@@ -257,24 +276,31 @@ def run_ours(args, rank, world):
     pairs_p = int(lgs.read_status(pipe.status)[L.ST_PAIRS])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    pipe.setup_backward()
     for _ in range(args.warmup):
         pipe.step(cfg_l)
+        pipe.stage_backward(cfg_l)
         pipe.step(cfg_p)
+        pipe.stage_backward(cfg_p)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     with Clocks(dev.index) as clk:
         st_l = time_steps(pipe, cfg_l, args.steps, flush)
         st_p = time_steps(pipe, cfg_p, args.steps, flush)
+        bw_l = time_steps(pipe, cfg_l, max(3, args.steps // 2), flush, backward=True)
+        bw_p = time_steps(pipe, cfg_p, max(3, args.steps // 2), flush, backward=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms_l = float(st_l.sum(1).mean())
     ms_p = float(st_p.sum(1).mean())
+    ms_lb = float(bw_l.sum(1).mean())
+    ms_pb = float(bw_p.sum(1).mean())
     if world > 1:
-        t = torch.tensor([ms_l, ms_p], device=dev)
+        t = torch.tensor([ms_l, ms_p, ms_lb, ms_pb], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_l, ms_p = t.tolist()
+        ms_l, ms_p, ms_lb, ms_pb = t.tolist()
     views = len(cams)
     P = lgs.n_pixels(cams)
     fps = world * views / (ms_l * 1e-3)
@@ -332,11 +358,17 @@ def run_ours(args, rank, world):
         "plain": {"frames_s": fps_p, "mpix_s": world * P / 1e6 / (ms_p * 1e-3), "ms_per_step": ms_p,
                   "render_ms": float(st_p.mean(0)[2]), "pairs": pairs_p},
         "render_speedup_vs_plain": float(st_p.mean(0)[2]) / render_ms,
+        "fwd_bwd": {"frames_s": world * views / (ms_lb * 1e-3), "mpix_s": world * P / 1e6 / (ms_lb * 1e-3),
+                    "ms_per_step": ms_lb, "backward_ms": float(bw_l.mean(0)[3]),
+                    "plain_frames_s": world * views / (ms_pb * 1e-3),
+                    "plain_mpix_s": world * P / 1e6 / (ms_pb * 1e-3), "plain_ms_per_step": ms_pb,
+                    "plain_backward_ms": float(bw_p.mean(0)[3]),
+                    "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step"},
         "roofline": {"bound": "alu", "kernel": "render_localgs", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "work": f"{pairs_l} pixel-Gaussian pairs x 19 FP32 flops",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
-        "gpu_launches": pipe.launches() * args.steps * 2,
+        "gpu_launches": pipe.launches() * (args.steps * 2 + 2 * max(3, args.steps // 2)) + 2 * 2 * max(3, args.steps // 2),
         "clocks": clk.summary(),
         "e2e": e2e,
     }

@@ -280,6 +280,137 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
     }
 }
 
+// Plain counterpart (comparison baseline): the plain forward's per-pixel
+// global-coordinate arithmetic and branches (power > 0 and alpha < 1/255
+// skipped, alpha = min(0.99, o exp(power))), every warp walking every Gaussian
+// of the tile list up to its largest contributor count (no warp mask, no
+// hoisting), gradients taken directly in (a, b, c, u, v, o, rgb) and reduced
+// with the same warp/CTA machinery as the Local-GS adjoint.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) render_bwd_plain(BwdParams p, Views vs) {
+    __shared__ float4 sXY[BWD_BATCH];
+    __shared__ float4 sCO[BWD_BATCH];
+    __shared__ float4 sC[BWD_BATCH];
+    __shared__ uint32_t sId[BWD_BATCH];
+    __shared__ float sG[BWD_BATCH][9];
+    __shared__ uint32_t sLast[8];
+
+    const uint32_t tile = blockIdx.x;
+    const int view = view_of_tile(vs, tile);
+    const ViewRec& c = vs.v[view];
+    const uint32_t lt = tile - c.tile_off;
+    const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = X0 + lane % TW, py = Y0 + warp * (TH / 8) + lane / TW;
+    const bool inside = px < c.W && py < c.H;
+    const float pxf = (float)px, pyf = (float)py;
+    const uint2 r = p.ranges[tile];
+
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, tail = 0.f;
+    uint32_t last = 0;
+    if (inside) {
+        const int64_t plane = (int64_t)c.W * c.H;
+        const int64_t pix = (int64_t)py * c.W + px;
+        const float* gr = p.dL_drgb + 3 * (int64_t)c.pix_off;
+        g0 = gr[pix];
+        g1 = gr[plane + pix];
+        g2 = gr[2 * plane + pix];
+        T = p.final_T[c.pix_off + pix];
+        last = p.n_contrib[c.pix_off + pix];
+        const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
+        tail = T * (c.bg[0] * g0 + c.bg[1] * g1 + c.bg[2] * g2 + gT);
+    }
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) sLast[warp] = wlast;
+    __syncthreads();
+    uint32_t tlast = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tlast = max(tlast, sLast[w]);
+
+    for (int end = (int)tlast; end > 0; end -= BWD_BATCH) {
+        const int begin = max(0, end - BWD_BATCH);
+        const int nb = end - begin;
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            const uint32_t pos = (uint32_t)(begin + threadIdx.x);
+            const uint32_t id = p.vals[r.x + pos];
+            sXY[threadIdx.x] = p.xy[id];
+            sCO[threadIdx.x] = p.conic[id];
+            const float4 col = p.rgb[id];
+            sC[threadIdx.x] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
+            sId[threadIdx.x] = id;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sG[threadIdx.x][k] = 0.f;
+        }
+        __syncthreads();
+        for (int g = min(nb, (int)wlast - begin) - 1; g >= 0; --g) {
+            const float4 col = sC[g];
+            const uint32_t pos = __float_as_uint(col.w);
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            float gb = 0.f;
+            if (pos <= last) {
+                const float4 xy = sXY[g];
+                const float4 co = sCO[g];
+                const float dx = __fadd_rn(xy.x - pxf, xy.z);
+                const float dy = __fadd_rn(xy.y - pyf, xy.w);
+                const float power = plain_power(co, dx, dy);
+                if (power <= 0.f) {
+                    const float G = __expf(power);
+                    const float alpha = fminf(0.99f, co.w * G);
+                    if (alpha >= 1.f / 255.f) {
+                        const float om = 1.f - alpha;
+                        const float Tk = T / om;
+                        const float w = alpha * Tk;
+                        v[6] = w * g0;
+                        v[7] = w * g1;
+                        gb = w * g2;
+                        const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
+                        const float dal = Tk * cg - tail / om;
+                        A0 = fmaf(alpha, col.x - A0, A0);
+                        A1 = fmaf(alpha, col.y - A1, A1);
+                        A2 = fmaf(alpha, col.z - A2, A2);
+                        T = Tk;
+                        if (co.w * G <= 0.99f) {
+                            const float dpw = dal * alpha;          // dL/dpower
+                            v[0] = -0.5f * dpw * dx * dx;           // a
+                            v[1] = -dpw * dx * dy;                  // b
+                            v[2] = -0.5f * dpw * dy * dy;           // c
+                            v[3] = -dpw * (co.x * dx + co.y * dy);  // u
+                            v[4] = -dpw * (co.y * dx + co.z * dy);  // v
+                            v[5] = dal * G;                         // o
+                        }
+                    }
+                }
+            }
+            const float s8 = warp_sum8_transposed(v);
+            const float s9 = warp_sum(gb);
+            if ((lane & 3) == 0) atomicAdd(&sG[g][lane >> 2], s8);
+            if (lane == 0) atomicAdd(&sG[g][8], s9);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            const int t = threadIdx.x;
+            const uint32_t id = sId[t];
+            if (sG[t][0] != 0.f || sG[t][1] != 0.f || sG[t][2] != 0.f || sG[t][5] != 0.f) {
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 0, sG[t][0]);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 1, sG[t][1]);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 2, sG[t][2]);
+                atomicAdd(p.g_conic + 4 * (int64_t)id + 3, sG[t][5]);
+                atomicAdd(p.g_xy + 2 * (int64_t)id + 0, sG[t][3]);
+                atomicAdd(p.g_xy + 2 * (int64_t)id + 1, sG[t][4]);
+            }
+            if (sG[t][6] != 0.f || sG[t][7] != 0.f || sG[t][8] != 0.f) {
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 0, sG[t][6]);
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 1, sG[t][7]);
+                atomicAdd(p.g_rgb + 3 * (int64_t)id + 2, sG[t][8]);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ preprocess adjoint
 struct PreBwdParams {
     const float* means;
@@ -506,8 +637,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) 
 }
 
 template <int TW, int TH>
-void launch_render_bwd(const BwdParams& bp, const Views& vs, cudaStream_t s) {
-    render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+void launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, cudaStream_t s) {
+    if (mode == LGS_MODE_PLAIN) render_bwd_plain<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+    else render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
 }
 
 }  // namespace lgs
@@ -555,9 +687,10 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     bp.g_xy = grads->xy2d;
     bp.g_conic = grads->conic2d;
     bp.g_rgb = grads->rgb2d;
-    if (cfg->tile_w == 16) launch_render_bwd<16, 16>(bp, vs, s);
-    else if (cfg->tile_w == 8) launch_render_bwd<8, 32>(bp, vs, s);
-    else launch_render_bwd<32, 8>(bp, vs, s);
+    if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
+    if (cfg->tile_w == 16) launch_render_bwd<16, 16>(bp, vs, cfg->mode, s);
+    else if (cfg->tile_w == 8) launch_render_bwd<8, 32>(bp, vs, cfg->mode, s);
+    else launch_render_bwd<32, 8>(bp, vs, cfg->mode, s);
     PreBwdParams pp;
     pp.means = g->means; pp.scales = g->scales; pp.quats = g->quats; pp.sh = g->sh; pp.n = g->n;
     pp.conic = reinterpret_cast<const float4*>(pre->conic);

@@ -112,4 +112,14 @@ __device__ __forceinline__ float ff_floor(ff a) {
     return f;
 }
 
+// Gaussian exponent of the plain (global-coordinate) kernels,
+// -1/2 (a dx^2 + c dy^2) - b dx dy, with explicit roundings so that the plain
+// forward and backward kernels evaluate it bit for bit alike.
+__device__ __forceinline__ float plain_power(float4 co, float dx, float dy) {
+    const float t1 = __fmul_rn(co.x, __fmul_rn(dx, dx));
+    const float t2 = __fmaf_rn(co.z, __fmul_rn(dy, dy), t1);
+    const float t3 = __fmul_rn(co.y, __fmul_rn(dx, dy));
+    return __fmaf_rn(-0.5f, t2, -t3);
+}
+
 }  // namespace lgs

@@ -133,14 +133,21 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 }
 
 // ------------------------------------------------------------------ Local-GS
-template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
-    __shared__ float4 sV[BATCH];   // (A, B, C, F), log2 domain
-    __shared__ float2 sDE[BATCH];  // (D, E)
-    __shared__ float4 sC[BATCH];   // (r, g, b, -)
-    __shared__ uint8_t sM[BATCH];  // warp-strip mask
+struct LocalSmem {
+    float4 sV[BATCH];   // (A, B, C, F), log2 domain
+    float2 sDE[BATCH];  // (D, E)
+    float4 sC[BATCH];   // (r, g, b, -)
+    uint8_t sM[BATCH];  // warp-strip mask
+};
 
-    const TileCtx t = tile_ctx<TW, TH>(vs, p, blockIdx.x);
+template <int TW, int TH, bool COUNT>
+__device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t tile,
+                                             LocalSmem& S) {
+    float4* sV = S.sV;
+    float2* sDE = S.sDE;
+    float4* sC = S.sC;
+    uint8_t* sM = S.sM;
+    const TileCtx t = tile_ctx<TW, TH>(vs, p, tile);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float Ox = (float)t.X0 + 0.5f * (TW - 1), Oy = (float)t.Y0 + 0.5f * (TH - 1);
     const float xl = (float)t.lx - 0.5f * (TW - 1), yl = (float)t.ly - 0.5f * (TH - 1);
@@ -215,6 +222,32 @@ __global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) 
                   (unsigned long long)pairs * 32ull);
 }
 
+// One CTA per tile.
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
+    __shared__ LocalSmem S;
+    localgs_tile<TW, TH, COUNT>(p, vs, blockIdx.x, S);
+}
+
+// Persistent CTAs: each pulls the next tile index from a work-queue counter
+// (status word LGS_ST_QUEUE, zeroed by the launcher) until all tiles are taken,
+// so uneven tile lists and uneven view sizes balance across the SMs.
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(256) render_localgs_persistent(RenderParams p, Views vs) {
+    __shared__ LocalSmem S;
+    __shared__ uint32_t s_tile;
+    unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(q, 1ull);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if (tile >= vs.n_tiles) break;
+        localgs_tile<TW, TH, COUNT>(p, vs, tile, S);
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ plain
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
@@ -246,7 +279,7 @@ __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
             const float dx = __fadd_rn(xy.x - pxf, xy.z);
             const float dy = __fadd_rn(xy.y - pyf, xy.w);
             const float4 co = sCO[g];
-            const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+            const float power = plain_power(co, dx, dy);
             if (power > 0.f) continue;
             const float alpha = fminf(0.99f, co.w * __expf(power));
             if (alpha < 1.f / 255.f) continue;
@@ -269,11 +302,26 @@ __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
 
 template <int TW, int TH>
 lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, bool count,
-                         cudaStream_t s) {
+                         bool persistent, cudaStream_t s) {
     const dim3 grid(vs.n_tiles), block(256);
     if (mode == LGS_MODE_PLAIN) {
         if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_plain<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
+    } else if (persistent) {
+        if (cudaMemsetAsync(p.status + LGS_ST_QUEUE, 0, sizeof(int64_t), s) != cudaSuccess)
+            return LGS_ERR_CUDA;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (count) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, true>, 256, 0);
+            const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+            render_localgs_persistent<TW, TH, true><<<g, block, 0, s>>>(p, vs);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, false>, 256, 0);
+            const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+            render_localgs_persistent<TW, TH, false><<<g, block, 0, s>>>(p, vs);
+        }
     } else {
         if (count) render_localgs<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_localgs<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
@@ -309,8 +357,9 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     p.out_n = n_contrib;
     p.status = d_status;
     const bool count = (cfg->flags & LGS_FLAG_COUNT) != 0;
+    const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, count, s);
-    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, count, s);
-    return launch_render<32, 8>(p, vs, cfg->mode, count, s);
+    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, count, persistent, s);
+    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, count, persistent, s);
+    return launch_render<32, 8>(p, vs, cfg->mode, count, persistent, s);
 }

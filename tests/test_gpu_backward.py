@@ -19,9 +19,9 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def _gpu_grads(sc, cams, g_rgb, g_T, tile=(16, 16)):
+def _gpu_grads(sc, cams, g_rgb, g_T, tile=(16, 16), mode="localgs"):
     g = lgs.to_device(sc)
-    res = lgs.render(g, cams, tile=tile)
+    res = lgs.render(g, cams, tile=tile, mode=mode)
     d_rgb = torch.from_numpy(np.ascontiguousarray(g_rgb, np.float32)).cuda().reshape(-1)
     d_T = None if g_T is None else torch.from_numpy(np.ascontiguousarray(g_T, np.float32)).cuda().reshape(-1)
     gr = lgs.render_bwd(g, cams, res["cfg"], res["pre"], res["vals"], res["ranges"], res["T_flat"],
@@ -30,9 +30,10 @@ def _gpu_grads(sc, cams, g_rgb, g_T, tile=(16, 16)):
     return {k: v.cpu().numpy() for k, v in gr.items()}, res
 
 
+@pytest.mark.parametrize("mode", ["localgs", "plain"])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
 @pytest.mark.parametrize("deg", [0, 3])
-def test_backward_matches_oracle_adjoint(tile, deg):
+def test_backward_matches_oracle_adjoint(tile, deg, mode):
     sc, cams = scenes.random_small(600, seed=71 + deg, width=90, height=70, sh_degree=deg,
                                    log_scale_mean=-2.6)
     cam = dict(cams[0])
@@ -41,7 +42,7 @@ def test_backward_matches_oracle_adjoint(tile, deg):
     H, W = cam["height"], cam["width"]
     g_rgb = rng.standard_normal((3, H, W))
     g_T = rng.standard_normal((H, W))
-    gg, _ = _gpu_grads(sc, [cam], g_rgb, g_T, tile)
+    gg, _ = _gpu_grads(sc, [cam], g_rgb, g_T, tile, mode)
     ref = oracle.backward(sc, cam, g_rgb, g_T, tile[0], tile[1])
     g2 = ref["g2d"]
     rep = {
@@ -52,7 +53,7 @@ def test_backward_matches_oracle_adjoint(tile, deg):
     }
     for k in ("means", "scales", "quats", "opacities", "sh"):
         rep[k] = _rel(gg[k], ref[k])
-    print(tile, deg, rep)
+    print(mode, tile, deg, rep)
     for k, v in rep.items():
         assert v <= REL, (k, v, rep)
 
