@@ -49,6 +49,8 @@ def parse():
                    help="only run warm-up + steps of the Local-GS pipeline (for ncu), no report")
     p.add_argument("--views", type=int, default=8, help="views of the outdoor workload (profiling)")
     p.add_argument("--mode", default="localgs", choices=["localgs", "plain"])
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-view batched workload")
+    p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
     return p.parse_args()
 
 
@@ -239,6 +241,56 @@ def time_steps(pipe, cfg, steps, flush, backward=False):
     return stage  # [steps, stages] ms
 
 
+def recorded_traffic(kernel="render_localgs_16x16"):
+    """DRAM bytes per launch from the committed ncu record, or None once the
+    kernel source no longer matches the profiled one."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, "paper_2606_16566_gb300", "csrc", "render.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] == rec["render_cu_sha256_prefix"]:
+            return rec["traffic_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def run_batched(dev, steps):
+    """The batched workload: 3M clustered SH3 Gaussians, 64 cameras of uneven
+    resolution; forward + backward captured in one CUDA graph, tile shape and
+    persistent launch picked by the autotuner, graph replays timed."""
+    import torch
+    from paper_2606_16566_gb300 import batch, lgs, scenes
+    sc, cams = scenes.batched()
+    g = lgs.to_device(sc, dev)
+    del sc
+    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False)
+    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True)
+    r.d_rgb.fill_(1.0 / r.d_rgb.numel())
+    r.capture()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ts = []
+    for i in range(max(3, steps // 4) + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r.graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append(e0.elapsed_time(e1))
+    st = r.check()
+    ms = float(np.mean(ts))
+    P = lgs.n_pixels(cams)
+    out = {"workload": "batched-3M-sh3-64-uneven-views-fwd+bwd-graph", "frames_s": len(cams) / (ms * 1e-3),
+           "mpix_s": P / 1e6 / (ms * 1e-3), "ms_per_step": ms, "instances_K": int(st[2]),
+           "tile": list(tune["tile"]), "persistent": tune["persistent"], "autotune": tune["timings"],
+           "replays": len(ts)}
+    del r, g
+    torch.cuda.empty_cache()
+    return out, len(ts)
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -256,8 +308,12 @@ def run_ours(args, rank, world):
         pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
         del probe
         cfg = lgs.config(tile, args.mode)
+        if args.backward:
+            pipe.setup_backward()
         for _ in range(args.warmup + args.steps):
             pipe.step(cfg)
+            if args.backward:
+                pipe.stage_backward(cfg)
         torch.cuda.synchronize()
         return
     cfg_l = lgs.config(tile, "localgs")
@@ -344,6 +400,9 @@ def run_ours(args, rank, world):
         e2e = {"value": world * views / (ms_e2e * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
+    batched, n_batched = (None, 0)
+    if not args.no_batched:
+        batched, n_batched = run_batched(dev, args.steps)
     if rank != 0:
         return
     line = {
@@ -365,12 +424,13 @@ def run_ours(args, rank, world):
                     "plain_backward_ms": float(bw_p.mean(0)[3]),
                     "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step"},
         "roofline": {"bound": "alu", "kernel": "render_localgs", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": recorded_traffic(),
                      "work": f"{pairs_l} pixel-Gaussian pairs x 19 FP32 flops",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "gpu_launches": pipe.launches() * (args.steps * 2 + 2 * max(3, args.steps // 2)) + 2 * 2 * max(3, args.steps // 2),
         "clocks": clk.summary(),
         "e2e": e2e,
+        "batched": batched,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)

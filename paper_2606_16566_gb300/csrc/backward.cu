@@ -208,19 +208,21 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
                     const uint32_t pos = __float_as_uint(col.w);
                     const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
                                      fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
+                    const bool contrib = pos <= last && pw >= LOG2_ALPHA_MIN_B;
+                    if (!__any_sync(0xffffffffu, contrib)) continue;   // nothing to reduce
                     const float e2 = ex2_approx_b(pw);
                     const float al = fminf(0.99f, e2);
                     float v[8];
                     float gb = 0.f;
-                    if (pos <= last && pw >= LOG2_ALPHA_MIN_B) {
-                        const float om = 1.f - al;
-                        const float Tk = T / om;
+                    if (contrib) {
+                        const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
+                        const float Tk = T * inv;
                         const float w = al * Tk;
                         v[5] = w * g0;
                         v[6] = w * g1;
                         gb = w * g2;
                         const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
-                        const float dal = Tk * cg - tail / om;
+                        const float dal = Tk * cg - tail * inv;
                         A0 = fmaf(al, col.x - A0, A0);
                         A1 = fmaf(al, col.y - A1, A1);
                         A2 = fmaf(al, col.z - A2, A2);
@@ -351,24 +353,26 @@ __global__ void __launch_bounds__(256) render_bwd_plain(BwdParams p, Views vs) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = 0.f;
             float gb = 0.f;
-            if (pos <= last) {
-                const float4 xy = sXY[g];
-                const float4 co = sCO[g];
-                const float dx = __fadd_rn(xy.x - pxf, xy.z);
-                const float dy = __fadd_rn(xy.y - pyf, xy.w);
-                const float power = plain_power(co, dx, dy);
-                if (power <= 0.f) {
-                    const float G = __expf(power);
-                    const float alpha = fminf(0.99f, co.w * G);
-                    if (alpha >= 1.f / 255.f) {
-                        const float om = 1.f - alpha;
-                        const float Tk = T / om;
+            const float4 xy = sXY[g];
+            const float4 co = sCO[g];
+            const float dx = __fadd_rn(xy.x - pxf, xy.z);
+            const float dy = __fadd_rn(xy.y - pyf, xy.w);
+            const float power = plain_power(co, dx, dy);
+            const float G = __expf(power);
+            const float alpha = fminf(0.99f, co.w * G);
+            const bool contrib = pos <= last && power <= 0.f && alpha >= 1.f / 255.f;
+            if (!__any_sync(0xffffffffu, contrib)) continue;           // nothing to reduce
+            if (contrib) {
+                {
+                    {
+                        const float inv = __fdividef(1.f, 1.f - alpha);
+                        const float Tk = T * inv;
                         const float w = alpha * Tk;
                         v[6] = w * g0;
                         v[7] = w * g1;
                         gb = w * g2;
                         const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
-                        const float dal = Tk * cg - tail / om;
+                        const float dal = Tk * cg - tail * inv;
                         A0 = fmaf(alpha, col.x - A0, A0);
                         A1 = fmaf(alpha, col.y - A1, A1);
                         A2 = fmaf(alpha, col.z - A2, A2);
