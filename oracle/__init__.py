@@ -63,7 +63,7 @@ def lib():
                                _u64p, _u32p, _u32p]
         L.orc_blend.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                 _u32p, _u32p, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
-                                _dp, _dp, _u32p, _u8p, _u32p, _u32p]
+                                _dp, _dp, _u32p, _u8p, _u32p, _u32p, _u8p]
         L.orc_hoist.argtypes = [ctypes.c_double] * 6 + [_dp]
         L.orc_warp_mask.restype = ctypes.c_uint32
         L.orc_warp_mask.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int] * 5
@@ -153,7 +153,7 @@ def sort(pre, cam, tile_w=16, tile_h=16, tile_offset=0, val_offset=0):
     return keys[:K], vals[:K], ranges
 
 
-def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
+def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, tile_mask=None):
     L = lib()
     W, H = cam["width"], cam["height"]
     bg = np.asarray(cam["bg"], np.float64)
@@ -168,16 +168,18 @@ def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD):
     L.orc_blend(W, H, tile_w, tile_h, _p(bg, _dp), _p(v, _u32p), _p(ranges, _u32p), 0,
                 _p(pre["uv"], _dp), _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
                 _p(pre["rgb"], _dp), _p(g, _dp), _p(out_rgb, _dp), _p(final_T, _dp),
-                _p(n_contrib, _u32p), _p(pguard, _u8p), _p(stop_pos, _u32p), _p(n_useful, _u32p))
+                _p(n_contrib, _u32p), _p(pguard, _u8p), _p(stop_pos, _u32p), _p(n_useful, _u32p),
+                None if tile_mask is None else _p(np.ascontiguousarray(tile_mask, np.uint8), _u8p))
     return {"rgb": out_rgb, "final_T": final_T, "n_contrib": n_contrib, "pguard": pguard,
             "stop_pos": stop_pos, "n_useful": n_useful}
 
 
-def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False):
-    """Full forward pass for one view: preprocess, sort, blend."""
+def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False, tile_mask=None):
+    """Full forward pass for one view: preprocess, sort, blend (optionally only
+    the pixels of the tiles selected by tile_mask)."""
     pre = preprocess(scene, cam, tile_w, tile_h, guard, exact)
     keys, vals, ranges = sort(pre, cam, tile_w, tile_h)
-    img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard)
+    img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard, tile_mask)
     img.update({"pre": pre, "keys": keys, "vals": vals, "ranges": ranges})
     return img
 

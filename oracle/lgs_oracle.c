@@ -331,18 +331,20 @@ int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_of
  * its relative guard band. stop_pos [H,W] (optional): list position (1-based)
  * of the Gaussian whose test_T fell below 1e-4, 0 if the pixel never stopped.
  * n_useful [H,W] (optional): blended Gaussians. vals index the per-Gaussian
- * arrays directly. */
+ * arrays directly. tile_mask [tiles] (optional): only pixels of tiles with a
+ * non-zero entry are computed (the others are left untouched). */
 void orc_blend(int W, int H, int tile_w, int tile_h, const double* bg,
                const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
                const double* uv, const double* conic, const double* opac, const double* rgb,
                const double* guard, double* out_rgb, double* final_T, uint32_t* n_contrib,
-               uint8_t* pguard, uint32_t* stop_pos, uint32_t* n_useful) {
+               uint8_t* pguard, uint32_t* stop_pos, uint32_t* n_useful, const uint8_t* tile_mask) {
     int gx = (W + tile_w - 1) / tile_w;
     const double a_min = 1.0 / 255.0;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
         int px = (int)(pix % W), py = (int)(pix / W);
         int64_t tile = tile_offset + (int64_t)(py / tile_h) * gx + px / tile_w;
+        if (tile_mask && !tile_mask[tile - tile_offset]) continue;   /* pixel not sampled */
         uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
         double T = 1.0, C[3] = { 0, 0, 0 };
         uint32_t last = 0, stop = 0, useful = 0;

@@ -134,7 +134,7 @@ def assert_image_parity(rep, what=""):
     assert rep["n_guard"] <= max(2, GUARD_FRAC * rep["n_pix"]), (what, rep)
 
 
-def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None):
+def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None, tile_mask=None):
     """One view of a GPU render (host copies) against the oracle.
 
     A pixel "disagrees" when its contributor count differs (compared by the
@@ -146,10 +146,12 @@ def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None):
     alpha >= 1/255 there. Disagreeing pixels are the guard items; the image
     tolerance applies to all others."""
     tw, th = tile
-    o = oracle_res if oracle_res is not None else oracle.render(scene, cam, tw, th)
+    o = oracle_res if oracle_res is not None else oracle.render(scene, cam, tw, th, tile_mask=tile_mask)
     W, H = cam["width"], cam["height"]
     g_vals, g_ranges = res_gpu_view["vals"], res_gpu_view["ranges"]
     bad = list_mismatch_tiles(g_vals, g_ranges, o["vals"], o["ranges"])
+    if tile_mask is not None:
+        bad = np.array([t for t in bad if tile_mask[t]], dtype=np.int64)
     guard_ids = np.nonzero(guard_gaussians(o["pre"]))[0]
     unexplained_tiles = explained_by_guards(bad, o["vals"], o["ranges"], g_vals, g_ranges, guard_ids)
     nc_g = res_gpu_view["n_contrib"].astype(np.int64)
@@ -177,6 +179,18 @@ def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None):
     err = np.abs(res_gpu_view["rgb"].astype(np.float64) - o["rgb"]).max(0)
     disagree = differ | (err > 1e-4)
     explained = (o["pguard"] != 0) | affected
+    if tile_mask is not None:                    # compare only the sampled tiles' pixels
+        sampled = tile_pixel_mask(np.nonzero(tile_mask)[0], W, H, tw, th)
+        disagree &= sampled
+        rep = image_report(res_gpu_view["rgb"][:, sampled][:, None, :], o["rgb"][:, sampled][:, None, :],
+                           disagree[sampled][None, :])
+        rep["n_guard"] = int(disagree.sum())
+        rep["n_unexplained"] = int((disagree & ~explained).sum())
+        rep["n_contrib_mismatch"] = int((differ & ~explained & sampled).sum())
+        rep["n_in_band"] = int(((o["pguard"] != 0) & sampled).sum())
+        rep["bad_tiles"] = len(bad)
+        rep["unexplained_tiles"] = unexplained_tiles
+        return rep, o
     rep = image_report(res_gpu_view["rgb"], o["rgb"], disagree)
     rep["n_guard"] = int(disagree.sum())
     rep["n_unexplained"] = int((disagree & ~explained).sum())
@@ -186,6 +200,24 @@ def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None):
     rep["bad_tiles"] = len(bad)
     rep["unexplained_tiles"] = unexplained_tiles
     return rep, o
+
+
+def tile_pixel_mask(tiles, W, H, tw, th):
+    gx = (W + tw - 1) // tw
+    m = np.zeros((H, W), bool)
+    for t in tiles:
+        ty, tx = divmod(int(t), gx)
+        m[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw] = True
+    return m
+
+
+def sample_tiles(cam, frac, seed, tile=(16, 16)):
+    tw, th = tile
+    nt = ((cam["width"] + tw - 1) // tw) * ((cam["height"] + th - 1) // th)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(nt, np.uint8)
+    mask[rng.choice(nt, max(1, int(frac * nt)), replace=False)] = 1
+    return mask
 
 
 def to_numpy_view(res, v, cams, n, tile):
