@@ -35,11 +35,6 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 2048
 
 constexpr int RADIX = 256;
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 (big-segment chunks)
-constexpr int PASS_ITEMS = 8;                          // tile-id passes: 2048 pairs per block
-constexpr int PASS_TILE = SORT_THREADS * PASS_ITEMS;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -227,143 +222,161 @@ __device__ __forceinline__ int64_t pass_count(const int64_t* status, int64_t n) 
     return status ? sort_count(status, n) : n;
 }
 
-// Stable digit ranks of a chunk of ITEMS*256 elements held in registers in
-// striped order (element j = i*256 + threadIdx.x). dg[i] in [0, 256); padding
-// elements carry digit 255 and come after every real one. On return rank[i]
-// counts the earlier elements of the chunk with the same digit and `total`
-// (thread t) is the chunk's count of digit t. Each round of 256 elements is
-// ranked inside warps with __match_any_sync; per-warp digit counters in shared
-// memory (double-buffered, cnt = 2 x 8 x 256 words) carry the prefix across
-// warps and rounds.
-template <int ITEMS>
-__device__ __forceinline__ void rank_chunk(const uint32_t (&dg)[ITEMS], uint16_t (&rank)[ITEMS],
-                                           uint32_t* cnt, uint32_t& total) {
-    const int t = threadIdx.x, warp = t >> 5;
-    const uint32_t lt = lanemask_lt();
+// ------------------------------------------------------------------ radix passes (onesweep)
+// A stable LSD pass moves (u32 key, u32 value) pairs by one 8-bit digit in a
+// single kernel. Each block takes the next tile index in launch order
+// (atomic counter), ranks its 4096 keys stably in shared memory, publishes its
+// per-digit counts, and obtains the count of every digit in all earlier tiles
+// by looking back over their published words (decoupled look-back, Merrill &
+// Garland): a word carries either the tile's own count (AGG) or its inclusive
+// prefix (PRE); the walk stops at the first PRE. A block only waits on tiles
+// that were handed out before its own and therefore are already running.
+// Every wait is bounded: after OS_SPIN_LIMIT polls the block records
+// LGS_ERR_TIMEOUT and continues. The digit bases of all passes come from one
+// histogram kernel over the input keys (digits of later passes are counted on
+// the same keys, since a pass only permutes them).
+constexpr int OS_THREADS = 256;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;   // 4096
+constexpr uint64_t OS_AGG = 1ull << 62;
+constexpr uint64_t OS_PRE = 2ull << 62;
+constexpr uint64_t OS_VAL = (1ull << 62) - 1;
+constexpr int OS_SPIN_LIMIT = 1 << 20;
+constexpr int OS_MAX_DIGITS = 4;
+
+// Per-digit-position histograms of the keys: ghist[p*256 + d] += count of
+// elements whose digit p (bits 8p..8p+7) is d, for p < npass.
+__global__ void __launch_bounds__(256) onesweep_histogram(const uint32_t* keys, const int64_t* status,
+                                                          int64_t count, int npass, uint32_t* ghist) {
+    __shared__ uint32_t h[OS_MAX_DIGITS * RADIX];
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
     __syncthreads();
-#pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; ++w) {
-        cnt[w * RADIX + t] = 0;
-        cnt[(SORT_THREADS / 32 + w) * RADIX + t] = 0;
+    const int64_t K = pass_count(status, count);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX + ((k >> (8 * p)) & 0xffu)], 1u);
     }
     __syncthreads();
-    uint32_t run = 0;
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        uint32_t* cb = cnt + (i & 1) * (SORT_THREADS / 32) * RADIX;
-        uint32_t* cn = cnt + ((i & 1) ^ 1) * (SORT_THREADS / 32) * RADIX;
-        const uint32_t d = dg[i];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t r = __popc(peers & lt);
-        if (r == 0) cb[warp * RADIX + d] = __popc(peers);
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < SORT_THREADS / 32; ++w) {
-            const uint32_t c = cb[w * RADIX + t];
-            cb[w * RADIX + t] = run;
-            run += c;
-            cn[w * RADIX + t] = 0;
-        }
-        __syncthreads();
-        rank[i] = (uint16_t)(cb[warp * RADIX + d] + r);
-    }
-    total = run;
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
-// ------------------------------------------------------------------ tile-id passes
-__global__ void __launch_bounds__(SORT_THREADS) radix_upsweep(const uint32_t* keys,
-                                                              const int64_t* status,
-                                                              int64_t capacity, int shift,
-                                                              uint32_t* hist, int nb) {
-    __shared__ uint32_t h[RADIX];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t K = pass_count(status, capacity);
-    const int64_t base = (int64_t)blockIdx.x * PASS_TILE;
-    const uint32_t lane = threadIdx.x & 31;
-    if (base < K) {
-#pragma unroll 4
-        for (int k = 0; k < PASS_ITEMS; ++k) {
-            const int64_t i = base + (int64_t)k * SORT_THREADS + threadIdx.x;
-            const uint32_t d = i < K ? ((keys[i] >> shift) & 0xffu) : 0x100u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (d < 0x100u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], __popc(peers));
-        }
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
-}
-
-// One block per digit: exclusive scan of that digit's row over blocks.
-__global__ void __launch_bounds__(1024) radix_scan_rows(uint32_t* hist, int nb,
-                                                        uint32_t* digit_total) {
+// In place: each digit position's 256 counts -> exclusive prefix (one block per position).
+__global__ void __launch_bounds__(RADIX) onesweep_bases(uint32_t* ghist) {
     __shared__ uint32_t ws[32];
-    uint32_t* row = hist + (int64_t)blockIdx.x * nb;
-    uint32_t carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < nb ? row[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<1024>(v, ws, tot);
-        if (i < nb) row[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
+    uint32_t* row = ghist + blockIdx.x * RADIX;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<RADIX>(row[threadIdx.x], ws, tot);
+    row[threadIdx.x] = ex;
 }
 
-struct DownSmem {
-    uint32_t base[RADIX];            // global output base per digit for this block
-    uint32_t start[RADIX];           // block-local start of each digit
-    uint32_t cnt[2 * (SORT_THREADS / 32) * RADIX];
+struct OneSmem {
+    uint32_t cnt[OS_THREADS / 32][RADIX];   // per-warp digit counters -> (digit, warp) offsets
     uint32_t ws[32];
-    uint32_t keys[PASS_TILE];
-    uint32_t vals[PASS_TILE];
+    uint32_t start[RADIX];   // block-local start of each digit
+    uint32_t base[RADIX];    // global output position of each digit's first element in this tile
+    uint32_t tile;
+    uint32_t keys[OS_TILE];
+    uint32_t vals[OS_TILE];
 };
 
-__global__ void __launch_bounds__(SORT_THREADS) radix_downsweep(
+// Keys are ranked warp by warp: warp w owns tile elements [w*512, (w+1)*512),
+// taken 32 at a time in order; __match_any_sync groups equal digits and the
+// warp's private counters give each key its rank among equal digits of the
+// warp's range, with no block barrier. A digit-major exclusive scan over
+// (digit, warp) then gives each (digit, warp) pair its place in the tile.
+__global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const int64_t* status, int64_t capacity, int shift,
-    const uint32_t* hist, int nb, const uint32_t* digit_total) {
+    uint32_t* __restrict__ vout, const int64_t* count_status, int64_t count, int shift,
+    const uint32_t* bases, unsigned long long* look, uint32_t* tile_counter, int64_t* err_status) {
+    constexpr int NW = OS_THREADS / 32;
+    constexpr int PER_WARP = OS_TILE / NW;      // 512
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
-    const int64_t K = pass_count(status, capacity);
-    const int64_t base = (int64_t)blockIdx.x * PASS_TILE;
-    if (base >= K) return;
-    const int n_valid = (int)min((int64_t)PASS_TILE, K - base);
-    const int t = threadIdx.x;
-    {
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<SORT_THREADS>(digit_total[t], S.ws, tot);
-        S.base[t] = ex + hist[(int64_t)t * nb + blockIdx.x];
-    }
-    uint32_t k[PASS_ITEMS], vv[PASS_ITEMS], dg[PASS_ITEMS];
+    OneSmem& S = *reinterpret_cast<OneSmem*>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    if (t == 0) S.tile = atomicAdd(tile_counter, 1u);
+    for (int d = lane; d < RADIX; d += 32) S.cnt[warp][d] = 0;
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    const int64_t K = pass_count(count_status, count);
+    const int64_t first = (int64_t)tile * OS_TILE;
+    if (first >= K) return;
+    const int n_valid = (int)min((int64_t)OS_TILE, K - first);
+    uint32_t k[OS_ITEMS], v[OS_ITEMS];
+    uint16_t rk[OS_ITEMS];
+    const int wbase = warp * PER_WARP;
 #pragma unroll
-    for (int i = 0; i < PASS_ITEMS; ++i) {
-        const int j = i * SORT_THREADS + t;
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const int j = wbase + i * 32 + lane;
         const bool ok = j < n_valid;
-        k[i] = ok ? kin[base + j] : 0xffffffffu;
-        vv[i] = ok ? vin[base + j] : 0u;
-        dg[i] = ok ? ((k[i] >> shift) & 0xffu) : 0xffu;
+        k[i] = ok ? kin[first + j] : 0xffffffffu;
+        v[i] = ok ? vin[first + j] : 0u;
     }
-    uint16_t rank[PASS_ITEMS];
-    uint32_t run;
-    rank_chunk<PASS_ITEMS>(dg, rank, S.cnt, run);
-    {
-        uint32_t tot;
-        S.start[t] = block_exclusive_scan<SORT_THREADS>(run, S.ws, tot);
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const int j = wbase + i * 32 + lane;
+        const uint32_t d = j < n_valid ? ((k[i] >> shift) & 0xffu) : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (d < 0x100u && lane == leader) b = S.cnt[warp][d];
+        b = __shfl_sync(0xffffffffu, b, leader);
+        rk[i] = (uint16_t)(b + __popc(peers & lt));
+        __syncwarp();
+        if (d < 0x100u && lane == leader) S.cnt[warp][d] = b + __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
+    // digit totals and per-(digit, warp) prefixes
+    uint32_t pre[NW], total = 0;
 #pragma unroll
-    for (int i = 0; i < PASS_ITEMS; ++i) {
-        const int j = i * SORT_THREADS + t;
+    for (int w = 0; w < NW; ++w) {
+        pre[w] = total;
+        total += S.cnt[w][t];
+    }
+    // publish this tile's counts, then look back for the prefix of earlier tiles
+    unsigned long long* my = look + (int64_t)tile * RADIX + t;
+    atomicExch(my, (unsigned long long)((tile == 0 ? OS_PRE : OS_AGG) | total));
+    uint64_t prefix = 0;
+    if (tile > 0) {
+        int64_t j = (int64_t)tile - 1;
+        int spins = 0;
+        while (j >= 0) {
+            const uint64_t w = *reinterpret_cast<volatile unsigned long long*>(look + j * RADIX + t);
+            const uint64_t f = w & ~OS_VAL;
+            if (f == 0) {
+                if (++spins > OS_SPIN_LIMIT) {
+                    report_error(err_status, LGS_ERR_TIMEOUT, (int64_t)tile);
+                    break;
+                }
+                continue;
+            }
+            prefix += w & OS_VAL;
+            if (f == OS_PRE) break;
+            --j;
+        }
+        atomicExch(my, (unsigned long long)(OS_PRE | (prefix + total)));
+    }
+    uint32_t all;
+    const uint32_t st = block_exclusive_scan<OS_THREADS>(total, S.ws, all);
+    S.start[t] = st;
+    S.base[t] = bases[t] + (uint32_t)prefix;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) S.cnt[w][t] = st + pre[w];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const int j = wbase + i * 32 + lane;
         if (j < n_valid) {
-            const uint32_t pos = S.start[dg[i]] + rank[i];
+            const uint32_t pos = S.cnt[warp][(k[i] >> shift) & 0xffu] + rk[i];
             S.keys[pos] = k[i];
-            S.vals[pos] = vv[i];
+            S.vals[pos] = v[i];
         }
     }
     __syncthreads();
-    for (int j = t; j < n_valid; j += SORT_THREADS) {
+    for (int j = t; j < n_valid; j += OS_THREADS) {
         const uint32_t key = S.keys[j];
         const uint32_t d = (key >> shift) & 0xffu;
         const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
@@ -426,8 +439,9 @@ struct SortWs {
     uint32_t* ak;          // [capacity] tile ids
     uint32_t* bk;          // [capacity]
     uint32_t* bv;          // [capacity] values (the caller's vals buffer is the other one)
-    uint32_t* hist;        // [256 * max(nb_entries, nb_instances)]
-    uint32_t* digit_total; // [256]
+    unsigned long long* look;  // [256 * max tiles of a pass] look-back words
+    uint32_t* counters;    // [8]: tile counter of the running pass
+    uint32_t* bases;       // [2 * OS_MAX_DIGITS * 256]: digit bases (entry sort, tile sort)
 };
 
 constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -440,19 +454,19 @@ constexpr size_t sort_ws_bytes(int64_t m, int64_t capacity) {
     const size_t mm = (size_t)(m > 0 ? m : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
-    const int64_t nb = ceil_div(m > capacity ? m : capacity, PASS_TILE);
+    const int64_t nt = ceil_div(m > capacity ? m : capacity, OS_TILE);
     return 6 * align_up(sizeof(uint32_t) * mm) +
            align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1)) +
            3 * align_up(sizeof(uint32_t) * cap) +
-           align_up(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1)) +
-           align_up(sizeof(uint32_t) * RADIX);
+           align_up(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1)) +
+           align_up(8 * sizeof(uint32_t)) + align_up(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
 }
 
 inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws) {
     const size_t mm = (size_t)(m > 0 ? m : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
-    const int64_t nb = ceil_div(m > capacity ? m : capacity, PASS_TILE);
+    const int64_t nt = ceil_div(m > capacity ? m : capacity, OS_TILE);
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align_up(bytes); return p; };
     char* e0 = take(sizeof(uint32_t) * mm);
@@ -465,8 +479,9 @@ inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws
     char* p2 = take(sizeof(uint32_t) * cap);
     char* p3 = take(sizeof(uint32_t) * cap);
     char* p4 = take(sizeof(uint32_t) * cap);
-    char* p6 = take(sizeof(uint32_t) * RADIX * (size_t)(nb > 0 ? nb : 1));
-    char* p7 = take(sizeof(uint32_t) * RADIX);
+    char* p6 = take(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1));
+    char* p7 = take(8 * sizeof(uint32_t));
+    char* p8 = take(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
     if (ws) {
         ws->ek = reinterpret_cast<uint32_t*>(e0);
         ws->ev = reinterpret_cast<uint32_t*>(e1);
@@ -478,8 +493,9 @@ inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws
         ws->ak = reinterpret_cast<uint32_t*>(p2);
         ws->bk = reinterpret_cast<uint32_t*>(p3);
         ws->bv = reinterpret_cast<uint32_t*>(p4);
-        ws->hist = reinterpret_cast<uint32_t*>(p6);
-        ws->digit_total = reinterpret_cast<uint32_t*>(p7);
+        ws->look = reinterpret_cast<unsigned long long*>(p6);
+        ws->counters = reinterpret_cast<uint32_t*>(p7);
+        ws->bases = reinterpret_cast<uint32_t*>(p8);
     }
     return off;
 }
@@ -490,17 +506,26 @@ inline int tile_passes(uint32_t n_tiles) {
     return bits == 0 ? 0 : (bits + 7) / 8;
 }
 
-// One stable LSD radix pass over u32 keys carrying u32 values. The element
-// count is the device instance count when `status` is given, else `count`.
+// Digit bases of `npass` LSD passes over `keys` (count from the device when
+// `status` is given): histogram + exclusive scan into bases[npass * 256].
+static void onesweep_prepare(const uint32_t* keys, const int64_t* status, int64_t count, int npass,
+                             uint32_t* bases, cudaStream_t s) {
+    cudaMemsetAsync(bases, 0, sizeof(uint32_t) * RADIX * npass, s);
+    onesweep_histogram<<<152 * 4, 256, 0, s>>>(keys, status, count, npass, bases);
+    onesweep_bases<<<npass, RADIX, 0, s>>>(bases);
+}
+
+// One stable LSD pass over u32 keys carrying u32 values (count from the device
+// instance count when `status` is given, else `count`).
 static void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-                       const int64_t* status, int64_t count, int shift, const SortWs* ws,
-                       cudaStream_t s) {
-    const int nb = (int)ceil_div(count, PASS_TILE);
-    if (nb == 0) return;
-    radix_upsweep<<<nb, SORT_THREADS, 0, s>>>(kin, status, count, shift, ws->hist, nb);
-    radix_scan_rows<<<RADIX, 1024, 0, s>>>(ws->hist, nb, ws->digit_total);
-    radix_downsweep<<<nb, SORT_THREADS, sizeof(DownSmem), s>>>(kin, vin, kout, vout, status, count,
-                                                             shift, ws->hist, nb, ws->digit_total);
+                       const int64_t* status, int64_t count, int shift, const uint32_t* bases,
+                       const SortWs* ws, int64_t* d_status, cudaStream_t s) {
+    const int64_t nt = ceil_div(count, OS_TILE);
+    if (nt == 0) return;
+    cudaMemsetAsync(ws->look, 0, sizeof(unsigned long long) * RADIX * (size_t)nt, s);
+    cudaMemsetAsync(ws->counters, 0, sizeof(uint32_t), s);
+    onesweep_pass<<<(unsigned)nt, OS_THREADS, sizeof(OneSmem), s>>>(
+        kin, vin, kout, vout, status, count, shift, bases, ws->look, ws->counters, d_status);
 }
 
 }  // namespace lgs
@@ -530,13 +555,14 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
         e = cudaMemsetAsync(d_status + LGS_ST_NUM_INSTANCES, 0, sizeof(int64_t), s);
         return cuda_status(e);
     }
-    cudaFuncSetAttribute(radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(DownSmem));
+    cudaFuncSetAttribute(onesweep_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(OneSmem));
     // 1. entries by depth
     depth_keys<<<152 * 8, 256, 0, s>>>(pre->tiles, pre->depth, m, ws->ek, ws->ev);
+    onesweep_prepare(ws->ek, nullptr, m, 4, ws->bases, s);
     uint32_t *k0 = ws->ek, *v0 = ws->ev, *k1 = ws->ek2, *v1 = ws->ev2;
     for (int shift = 0; shift < 32; shift += 8) {
-        radix_pass(k0, v0, k1, v1, nullptr, m, shift, ws, s);
+        radix_pass(k0, v0, k1, v1, nullptr, m, shift, ws->bases + RADIX * (shift / 8), ws, d_status, s);
         uint32_t* t = k0; k0 = k1; k1 = t;
         t = v0; v0 = v1; v1 = t;
     }
@@ -555,8 +581,10 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     emit_pairs<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect,
                                                           m, n, d_status, capacity, *vs, ka, va);
     // 4. tile-id passes over the K instances
+    if (passes > 0) onesweep_prepare(ka, d_status, capacity, passes, ws->bases + OS_MAX_DIGITS * RADIX, s);
     for (int p = 0; p < passes; ++p) {
-        radix_pass(ka, va, kb, vb, d_status, capacity, 8 * p, ws, s);
+        radix_pass(ka, va, kb, vb, d_status, capacity, 8 * p, ws->bases + (OS_MAX_DIGITS + p) * RADIX, ws,
+                   d_status, s);
         uint32_t* t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }
