@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--mode", default="localgs", choices=["localgs", "plain"])
     p.add_argument("--no-batched", action="store_true", help="skip the 64-view batched workload")
     p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
+    p.add_argument("--tight", action="store_true", help="with --profile: tight-box emission")
     return p.parse_args()
 
 
@@ -208,15 +209,15 @@ class Pipeline:
                             self.d_rgb, None, self.grads, self.status)
 
     def launches(self):
-        """Kernels of one step: preprocess; depth keys + 4 entry passes (3 kernels
-        each); gather + 3 scan kernels; emission; tile-id passes; ranges; render."""
-        from math import ceil
+        """Kernels of one forward step: preprocess; depth keys, digit histogram +
+        bases, 4 entry passes; gather + 3 scan kernels; emission; digit histogram
+        + bases and one onesweep pass per tile-id byte; ranges; render."""
         nt = self.ranges.shape[0]
         bits = 0
         while (1 << bits) < nt:
             bits += 1
-        tile_passes = ceil(bits / 8)
-        return 1 + 1 + 4 * 3 + 1 + 3 + 1 + 3 * tile_passes + 1 + 1
+        tile_passes = (bits + 7) // 8
+        return 1 + (1 + 2 + 4) + (1 + 3) + 1 + ((2 + tile_passes) if tile_passes else 0) + 1 + 1
 
 
 def time_steps(pipe, cfg, steps, flush, backward=False):
@@ -247,8 +248,9 @@ def recorded_traffic(kernel="render_localgs_16x16"):
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
-        src = open(os.path.join(ROOT, "paper_2606_16566_gb300", "csrc", "render.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] == rec["render_cu_sha256_prefix"]:
+        src = b"".join(open(os.path.join(ROOT, "paper_2606_16566_gb300", "csrc", f), "rb").read()
+                       for f in ("render.cu", "common.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] == rec["source_sha256_prefix"]:
             return rec["traffic_bytes_per_launch"]
     except (OSError, KeyError, ValueError):
         pass
@@ -307,7 +309,7 @@ def run_ours(args, rank, world):
         probe = lgs.render(g, cams, tile=tile)
         pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
         del probe
-        cfg = lgs.config(tile, args.mode)
+        cfg = lgs.config(tile, args.mode, L.FLAG_TIGHT if args.tight else 0)
         if args.backward:
             pipe.setup_backward()
         for _ in range(args.warmup + args.steps):
@@ -316,58 +318,79 @@ def run_ours(args, rank, world):
                 pipe.stage_backward(cfg)
         torch.cuda.synchronize()
         return
-    cfg_l = lgs.config(tile, "localgs")
-    cfg_p = lgs.config(tile, "plain")
+    TF = L.FLAG_TIGHT
+    variants = {"localgs": lgs.config(tile, "localgs"), "plain": lgs.config(tile, "plain"),
+                "localgs_tight": lgs.config(tile, "localgs", TF), "plain_tight": lgs.config(tile, "plain", TF)}
 
     # discover K and size the instance buffers once (outside the timed region)
     probe = lgs.render(g, cams, tile=tile)
     K = probe["K"]
     pipe = Pipeline(g, cams, tile, int(K * 1.05) + 1024)
     del probe
-    # schedule work of the Local-GS render (pixel-Gaussian pairs), counted once
-    pipe.step(lgs.config(tile, "localgs", flags=L.FLAG_COUNT))
-    st = lgs.read_status(pipe.status)
-    pairs_l = int(st[L.ST_PAIRS])
-    pipe.step(lgs.config(tile, "plain", flags=L.FLAG_COUNT))
-    pairs_p = int(lgs.read_status(pipe.status)[L.ST_PAIRS])
+    # schedule work of the Local-GS render (pixel-Gaussian pairs) and K, counted once
+    counts = {}
+    for name, cfg in variants.items():
+        pipe.step(lgs.config(tile, "plain" if name.startswith("plain") else "localgs",
+                             cfg.flags | L.FLAG_COUNT))
+        st = lgs.read_status(pipe.status)
+        if st[L.ST_CODE] != 0:
+            raise L.LgsError(int(st[L.ST_CODE]), f"device status in {name}")
+        counts[name] = {"pairs": int(st[L.ST_PAIRS]), "K": int(st[L.ST_NUM_INSTANCES])}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     pipe.setup_backward()
     for _ in range(args.warmup):
-        pipe.step(cfg_l)
-        pipe.stage_backward(cfg_l)
-        pipe.step(cfg_p)
-        pipe.stage_backward(cfg_p)
+        for cfg in variants.values():
+            pipe.step(cfg)
+            pipe.stage_backward(cfg)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    n_bw = max(3, args.steps // 2)
+    fwd, fb = {}, {}
     with Clocks(dev.index) as clk:
-        st_l = time_steps(pipe, cfg_l, args.steps, flush)
-        st_p = time_steps(pipe, cfg_p, args.steps, flush)
-        bw_l = time_steps(pipe, cfg_l, max(3, args.steps // 2), flush, backward=True)
-        bw_p = time_steps(pipe, cfg_p, max(3, args.steps // 2), flush, backward=True)
+        for name, cfg in variants.items():
+            fwd[name] = time_steps(pipe, cfg, args.steps, flush)
+            fb[name] = time_steps(pipe, cfg, n_bw, flush, backward=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms_l = float(st_l.sum(1).mean())
-    ms_p = float(st_p.sum(1).mean())
-    ms_lb = float(bw_l.sum(1).mean())
-    ms_pb = float(bw_p.sum(1).mean())
+    st = lgs.read_status(pipe.status)
+    if st[L.ST_CODE] != 0:
+        raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
+    ms = {n: float(fwd[n].sum(1).mean()) for n in variants}
+    ms_b = {n: float(fb[n].sum(1).mean()) for n in variants}
     if world > 1:
-        t = torch.tensor([ms_l, ms_p, ms_lb, ms_pb], device=dev)
+        names = list(variants)
+        t = torch.tensor([ms[n] for n in names] + [ms_b[n] for n in names], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_l, ms_p, ms_lb, ms_pb = t.tolist()
+        vals = t.tolist()
+        ms = dict(zip(names, vals[:len(names)]))
+        ms_b = dict(zip(names, vals[len(names):]))
     views = len(cams)
     P = lgs.n_pixels(cams)
+    # headline: the faster of the two Local-GS emissions (both reported)
+    head = min(("localgs", "localgs_tight"), key=lambda n: ms[n])
+    ms_l = ms[head]
     fps = world * views / (ms_l * 1e-3)
-    fps_p = world * views / (ms_p * 1e-3)
-    stage_ms = st_l.mean(0)
+    stage_ms = fwd[head].mean(0)
     render_ms = float(stage_ms[2])
     sm_max = 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at max SM clock
-    flops = pairs_l * 19.0
+    flops = counts[head]["pairs"] * 19.0
     achieved = flops / (render_ms * 1e-3) / 1e12
+    cfg_l = variants[head]
+
+    def summary(name):
+        f, b = fwd[name].mean(0), fb[name].mean(0)
+        return {"frames_s": world * views / (ms[name] * 1e-3), "mpix_s": world * P / 1e6 / (ms[name] * 1e-3),
+                "ms_per_step": ms[name],
+                "stage_ms": {"preprocess": float(f[0]), "sort": float(f[1]), "render": float(f[2])},
+                "fwd_bwd": {"frames_s": world * views / (ms_b[name] * 1e-3),
+                            "mpix_s": world * P / 1e6 / (ms_b[name] * 1e-3), "ms_per_step": ms_b[name],
+                            "backward_ms": float(b[3])},
+                "instances_K": counts[name]["K"], "pairs": counts[name]["pairs"]}
 
     # end to end: host scene -> device, pipeline, image -> host, every step
     e2e = None
@@ -405,29 +428,29 @@ def run_ours(args, rank, world):
         batched, n_batched = run_batched(dev, args.steps)
     if rank != 0:
         return
+    emission = "tight" if head.endswith("tight") else "rect"
+    plain_same = "plain_tight" if emission == "tight" else "plain"
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n, "tile": args.tile,
-                   "instances_K": K, "l2": "flushed between steps (256 MB write, outside the events)",
+                   "emission": emission, "instances_K": counts[head]["K"],
+                   "l2": "flushed between steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
-        "mpix_s": world * views * (P / views) / 1e6 / (ms_l * 1e-3),
+        "mpix_s": world * P / 1e6 / (ms_l * 1e-3),
         "stage_ms": {"preprocess": float(stage_ms[0]), "sort": float(stage_ms[1]), "render": render_ms},
-        "plain": {"frames_s": fps_p, "mpix_s": world * P / 1e6 / (ms_p * 1e-3), "ms_per_step": ms_p,
-                  "render_ms": float(st_p.mean(0)[2]), "pairs": pairs_p},
-        "render_speedup_vs_plain": float(st_p.mean(0)[2]) / render_ms,
-        "fwd_bwd": {"frames_s": world * views / (ms_lb * 1e-3), "mpix_s": world * P / 1e6 / (ms_lb * 1e-3),
-                    "ms_per_step": ms_lb, "backward_ms": float(bw_l.mean(0)[3]),
-                    "plain_frames_s": world * views / (ms_pb * 1e-3),
-                    "plain_mpix_s": world * P / 1e6 / (ms_pb * 1e-3), "plain_ms_per_step": ms_pb,
-                    "plain_backward_ms": float(bw_p.mean(0)[3]),
-                    "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step"},
+        "fwd_bwd": summary(head)["fwd_bwd"],
+        "plain": summary(plain_same),
+        "render_speedup_vs_plain": float(fwd[plain_same].mean(0)[2]) / render_ms,
+        "variants": {n: summary(n) for n in variants},
+        "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step",
         "roofline": {"bound": "alu", "kernel": "render_localgs", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "work": f"{pairs_l} pixel-Gaussian pairs x 19 FP32 flops",
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
-        "gpu_launches": pipe.launches() * (args.steps * 2 + 2 * max(3, args.steps // 2)) + 2 * 2 * max(3, args.steps // 2),
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic("render_localgs_16x16_" + emission),
+                     "work": f"{counts[head]['pairs']} pixel-Gaussian pairs x 19 FP32 flops",
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)"},
+        "gpu_launches": len(variants) * (pipe.launches() * (args.steps + n_bw) + 2 * n_bw),
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched": batched,

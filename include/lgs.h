@@ -60,6 +60,7 @@ typedef int32_t lgs_status;
 #define LGS_ERR_NONFINITE 5    /* reserved: non-finite inputs are counted, not fatal */
 #define LGS_ERR_TIMEOUT 6      /* a bounded device-side wait gave up */
 #define LGS_ERR_CUDA 7         /* a CUDA launch failed (detail = cudaError_t) */
+#define LGS_ERR_INTERNAL 8     /* device-side consistency check failed (a library bug); outputs are invalid */
 
 #define LGS_MAX_VIEWS 64
 #define LGS_MAX_SH_DEGREE 3
@@ -108,6 +109,16 @@ typedef struct {
 
 #define LGS_FLAG_COUNT 1        /* render also counts its schedule's pixel-Gaussian pairs into d_status[LGS_ST_PAIRS] */
 #define LGS_FLAG_PERSISTENT 2   /* render with persistent CTAs pulling tiles from a work queue */
+/* Tight-box emission (lgs_sort): an entry is duplicated only into the tiles of
+ * its rect that the conservative tight box of Sec. III-C2 reaches, evaluated
+ * per tile column strip (the ellipse alpha = 1/255 widened to
+ * tau' = 1.001 tau + 0.02 and by 1/64 px; the same box whose rows give the
+ * render's warp mask), instead of every tile of the rect. A dropped
+ * (Gaussian, tile) pair has alpha < 1/255 at every pixel of the tile, so
+ * images are unchanged; K, the tile lists and the list positions in n_contrib
+ * shrink. lgs_sort then also reads pre->xy and pre->conic. The other entry
+ * points ignore the flag (they follow the lists they are given). */
+#define LGS_FLAG_TIGHT 4
 
 /* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}; 8 warps per tile, each a
  * tile_w x tile_h/8 strip), render mode and flags. batch = Gaussians staged in
@@ -174,9 +185,10 @@ size_t lgs_sort_workspace_size(int64_t m, int64_t capacity);
  * surviving primitives across intersecting tiles into 64-bit key-value pairs,
  * which are sorted by GPU radix sort to produce ... tile ranges"):
  * exclusive scan of tiles, emission of key = (tile_id << 32) | bits(depth) and
- * value = v*N + i in Gaussian order (tiles row-major inside the rect), a stable
- * radix sort by key (ties keep emission order), and per-tile ranges
- * [start, end) (0,0 for empty tiles).
+ * value = v*N + i in Gaussian order (tiles row-major inside the rect; with
+ * LGS_FLAG_TIGHT only the tiles the tight box reaches), a stable radix sort by
+ * key (ties keep emission order), and per-tile ranges [start, end) (0,0 for
+ * empty tiles).
  * keys [capacity] u64 (may be NULL: the sorted keys are then not written),
  * vals [capacity] u32, ranges [n_tiles_total,2] u32 (all device, caller-owned,
  * keys and ranges 8-B aligned). K is written to d_status[LGS_ST_NUM_INSTANCES]; if

@@ -28,10 +28,10 @@ _LIB = None
 # (relative), near plane (relative), depth float32 rounding midpoint
 # (relative; 0 because camera-space z is reproduced bit for bit), det
 # (relative), alpha against 1/255 (relative), T(1-alpha) against 1e-4
-# (relative).
-DEFAULT_GUARD = np.array([1e-4, 2e-6, 1e-6, 0.0, 1e-6, 1e-4, 1e-4], dtype=np.float64)
+# (relative), tight-box level tau' (relative) and tight-box span ends (px).
+DEFAULT_GUARD = np.array([1e-4, 2e-6, 1e-6, 0.0, 1e-6, 1e-4, 1e-4, 1e-4, 2e-3], dtype=np.float64)
 
-GF_RECT, GF_RADIUS, GF_NEAR, GF_DEPTH, GF_DET = 1, 2, 4, 8, 16
+GF_RECT, GF_RADIUS, GF_NEAR, GF_DEPTH, GF_DET, GF_TIGHT = 1, 2, 4, 8, 16, 32
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -55,12 +55,16 @@ def lib():
         L.orc_cov3d.argtypes = [_dp, _dp, _dp]
         L.orc_ewa.argtypes = [_dp, _dp, _dp, _dp]
         L.orc_preprocess.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
-                                     _dp, ctypes.c_int, ctypes.c_int, _dp,
+                                     _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                      _dp, _dp, _u32p, _dp, _i32p, _i32p, _i64p, _dp, _u8p, _u8p]
         L.orc_sort.restype = ctypes.c_int64
         L.orc_sort.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                ctypes.c_uint32, _i32p, _i64p, _u32p, ctypes.c_int64,
-                               _u64p, _u32p, _u32p]
+                               _u64p, _u32p, _u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               _dp, _dp, _dp]
+        L.orc_tight_rows.restype = ctypes.c_int
+        L.orc_tight_rows.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + \
+            [_i32p, _i32p, _i32p]
         L.orc_blend.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                 _u32p, _u32p, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
                                 _dp, _dp, _u32p, _u8p, _u32p, _u32p, _u8p]
@@ -113,7 +117,7 @@ def sh_degree_of(scene) -> int:
     return int(round(k ** 0.5)) - 1
 
 
-def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False):
+def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False, tight=False):
     L = lib()
     n = scene["means"].shape[0]
     deg = sh_degree_of(scene)
@@ -128,16 +132,19 @@ def preprocess(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=Fals
         "gflags": np.zeros(n, np.uint8),
     }
     L.orc_preprocess(n, deg, _p(m, _dp), _p(s, _dp), _p(q, _dp), _p(o, _dp), _p(sh, _dp),
-                     _p(c, _dp), tile_w, tile_h, _p(g, _dp),
+                     _p(c, _dp), tile_w, tile_h, int(bool(tight)), _p(g, _dp),
                      _p(out["uv"], _dp), _p(out["depth"], _dp), _p(out["depth_bits"], _u32p),
                      _p(out["conic"], _dp), _p(out["radius"], _i32p), _p(out["rect"], _i32p),
                      _p(out["tiles"], _i64p), _p(out["rgb"], _dp), _p(out["clamped"], _u8p),
                      _p(out["gflags"], _u8p))
     out["opacity"] = o
+    out["tight"] = bool(tight)
     return out
 
 
 def sort(pre, cam, tile_w=16, tile_h=16, tile_offset=0, val_offset=0):
+    """Duplicate + stable sort; tight-box emission when pre came from
+    preprocess(..., tight=True)."""
     L = lib()
     W, H = cam["width"], cam["height"]
     gx, gy = (W + tile_w - 1) // tile_w, (H + tile_h - 1) // tile_h
@@ -146,11 +153,14 @@ def sort(pre, cam, tile_w=16, tile_h=16, tile_offset=0, val_offset=0):
     keys = np.zeros(max(K, 1), np.uint64)
     vals = np.zeros(max(K, 1), np.uint32)
     ranges = np.zeros((gx * gy, 2), np.uint32)
+    tight = bool(pre.get("tight", False))
     r = L.orc_sort(n, gx, gy, tile_offset, val_offset, _p(pre["rect"], _i32p),
                    _p(pre["tiles"], _i64p), _p(pre["depth_bits"], _u32p), K,
-                   _p(keys, _u64p), _p(vals, _u32p), _p(ranges, _u32p))
-    assert r == K
-    return keys[:K], vals[:K], ranges
+                   _p(keys, _u64p), _p(vals, _u32p), _p(ranges, _u32p), int(tight), tile_w, tile_h,
+                   _p(np.ascontiguousarray(pre["uv"]), _dp), _p(np.ascontiguousarray(pre["conic"]), _dp),
+                   _p(np.ascontiguousarray(pre["opacity"]), _dp))
+    assert 0 <= r <= K and (tight or r == K)
+    return keys[:r], vals[:r], ranges
 
 
 def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, tile_mask=None):
@@ -174,10 +184,12 @@ def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, til
             "stop_pos": stop_pos, "n_useful": n_useful}
 
 
-def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False, tile_mask=None):
+def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False, tile_mask=None,
+           tight=False):
     """Full forward pass for one view: preprocess, sort, blend (optionally only
-    the pixels of the tiles selected by tile_mask)."""
-    pre = preprocess(scene, cam, tile_w, tile_h, guard, exact)
+    the pixels of the tiles selected by tile_mask; tight-box emission with
+    tight=True)."""
+    pre = preprocess(scene, cam, tile_w, tile_h, guard, exact, tight)
     keys, vals, ranges = sort(pre, cam, tile_w, tile_h)
     img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard, tile_mask)
     img.update({"pre": pre, "keys": keys, "vals": vals, "ranges": ranges})
@@ -192,6 +204,15 @@ def hoist(a, b, c, o, dx, dy):
 
 def warp_mask(a, b, c, o, mux, muy, X0, Y0, tile_w=16, tile_h=16, n_warps=8):
     return int(lib().orc_warp_mask(a, b, c, o, mux, muy, X0, Y0, tile_w, tile_h, n_warps))
+
+
+def tight_rows(a, b, c, o, mux, muy, X0, ry0, ry1, tile_w=16, tile_h=16, band_tau=0.0, band_px=0.0):
+    """Kept tile rows (lo, hi, count, guard) of one column strip under the
+    tight-box emission rule."""
+    lo, hi, gd = ctypes.c_int32(0), ctypes.c_int32(-1), ctypes.c_int32(0)
+    k = lib().orc_tight_rows(a, b, c, o, mux, muy, X0, tile_w, tile_h, ry0, ry1, band_tau, band_px,
+                             ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(gd))
+    return lo.value, hi.value, int(k), bool(gd.value)
 
 
 def localgs_pairs(res, cam, tile_w=16, tile_h=16, n_warps=8):
@@ -254,7 +275,8 @@ def ewa(cam, t, Sig):
     return out
 
 
-__all__ = ["render", "backward", "preprocess", "sort", "blend", "hoist", "warp_mask", "localgs_pairs",
+__all__ = ["render", "backward", "preprocess", "sort", "blend", "hoist", "warp_mask", "tight_rows",
+           "localgs_pairs",
            "sh_basis", "quat_to_rot", "cov3d", "ewa", "num_threads", "cam_array",
            "DEFAULT_GUARD"]
 os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")

@@ -32,6 +32,9 @@
  *                    stack stop rule, invariants, brute force without tiling)
  *   orc_hoist        pinned (identity with the direct quadratic form)
  *   orc_warp_mask    pinned (brute-force sampling of the ellipse)
+ *   orc_tight_rows   pinned (brute-force alpha over every pixel of the rect:
+ *                    no dropped tile holds a pixel with alpha >= 1/255; every
+ *                    kept tile holds a pixel inside the widened ellipse)
  *   orc_backward     pinned (central finite differences of orc_* forward)
  */
 #include <math.h>
@@ -53,10 +56,10 @@ enum { CAM_W = 0, CAM_H, CAM_FX, CAM_FY, CAM_CX, CAM_CY, CAM_R, CAM_T = 15,
 
 /* guard thresholds (see orc_preprocess / orc_blend) */
 enum { G_RECT_PX = 0, G_RADIUS_REL, G_NEAR_REL, G_DEPTH_REL, G_DET_REL,
-       G_ALPHA_REL, G_STOP_REL, G_SIZE };
+       G_ALPHA_REL, G_STOP_REL, G_TIGHT_TAU_REL, G_TIGHT_PX, G_SIZE };
 
 /* per-Gaussian guard flag bits */
-enum { GF_RECT = 1, GF_RADIUS = 2, GF_NEAR = 4, GF_DEPTH = 8, GF_DET = 16 };
+enum { GF_RECT = 1, GF_RADIUS = 2, GF_NEAR = 4, GF_DEPTH = 8, GF_DET = 16, GF_TIGHT = 32 };
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -176,6 +179,68 @@ static double int_dist_in(double q, int lo, int hi) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Tight-box tile rows (Sec. III-C2 tight box applied to emission; the
+ * Speedy-Splat / AdR-style tightening the paper composes with, Sec. II).
+ * For the column strip of pixel columns X0 .. X0 + tile_w - 1: the ellipse
+ *   a x~^2 + 2 b x~ y~ + c y~^2 = tau',  tau' = 1.001 * 2 ln(255 o) + 0.02
+ * (the alpha = 1/255 level set, widened by the library's stated margin) is
+ * cut to the strip's x-range, its lowest and highest points over that range
+ * found by Cases A/B/C (as in orc_warp_mask), and the span widened by 1/64 px
+ * at both ends. The kept pixel rows are ceil(lower) .. floor(upper); the kept
+ * tile rows of the rect rows [ry0, ry1) are those holding a kept pixel row.
+ * Returns the number of kept tile rows, [*lo, *hi] their range.
+ * `widen` moves the decision boundaries outward (> 0) or inward (< 0) by
+ * |widen| * (tau' relative band) and |widen| * (pixel band), for the guard. */
+static int tight_rows_at(double a, double b, double c, double o, double mux, double muy,
+                         int X0, int tile_w, int tile_h, int ry0, int ry1,
+                         double tau_rel, double px, int* lo, int* hi) {
+    double tau = 1.001 * (2.0 * log(255.0 * o)) + 0.02;
+    tau = tau * (1.0 + tau_rel) + tau_rel * 1e-3;
+    if (!(tau > 0.0)) return 0;
+    double det = a * c - b * b;
+    double xr = sqrt(c * tau / det);
+    double x0 = X0 - mux, x1 = X0 + tile_w - 1 - mux;
+    if (x1 < -xr - px || x0 > xr + px) return 0;
+    if (x0 < -xr) x0 = -xr;
+    if (x1 > xr) x1 = xr;
+    if (x0 > x1) { double m = 0.5 * (x0 + x1); x0 = x1 = m; }   /* inside the px band only */
+    double dy = sqrt(a * tau / det);
+    double ymax, ymin;
+    if (-b * dy < a * x0)      ymax = (-b * x0 + sqrt(fmax(0.0, c * tau - det * x0 * x0))) / c;
+    else if (-b * dy > a * x1) ymax = (-b * x1 + sqrt(fmax(0.0, c * tau - det * x1 * x1))) / c;
+    else                       ymax = dy;
+    if (b * dy < a * x0)       ymin = (-b * x0 - sqrt(fmax(0.0, c * tau - det * x0 * x0))) / c;
+    else if (b * dy > a * x1)  ymin = (-b * x1 - sqrt(fmax(0.0, c * tau - det * x1 * x1))) / c;
+    else                       ymin = -dy;
+    double P = ceil(muy + ymin - 1.0 / 64.0 - px);
+    double Q = floor(muy + ymax + 1.0 / 64.0 + px);
+    if (P > Q) return 0;
+    int l = ry0, h = ry1 - 1;
+    double tl = floor(P / tile_h), th = floor(Q / tile_h);
+    if (tl > l) l = (int)tl;
+    if (th < h) h = (int)th;
+    *lo = l; *hi = h;
+    return h >= l ? h - l + 1 : 0;
+}
+
+/* Kept tile rows of one column strip (central decision) and, in *guard, 1 if
+ * the decision changes anywhere inside the guard band (boundaries moved by
+ * +-band_tau relatively on tau' and +-band_px pixels). */
+int orc_tight_rows(double a, double b, double c, double o, double mux, double muy,
+                   int X0, int tile_w, int tile_h, int ry0, int ry1,
+                   double band_tau, double band_px, int* lo, int* hi, int* guard) {
+    int l = 0, h = -1, l1 = 0, h1 = -1, l2 = 0, h2 = -1;
+    int n = tight_rows_at(a, b, c, o, mux, muy, X0, tile_w, tile_h, ry0, ry1, 0.0, 0.0, &l, &h);
+    int n_out = tight_rows_at(a, b, c, o, mux, muy, X0, tile_w, tile_h, ry0, ry1,
+                              band_tau, band_px, &l1, &h1);
+    int n_in = tight_rows_at(a, b, c, o, mux, muy, X0, tile_w, tile_h, ry0, ry1,
+                             -band_tau, -band_px, &l2, &h2);
+    *lo = l; *hi = h;
+    if (guard) *guard = (n_out != n_in) || (n_out > 0 && (l1 != l2 || h1 != h2));
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
 /* Preprocess: one Gaussian per iteration, standard 3DGS semantics.
  * Outputs (per Gaussian i):
  *   uv[2i..]      projected mean (pixel units, pixel (i,j) sampled at (i,j))
@@ -184,12 +249,14 @@ static double int_dist_in(double q, int lo, int hi) {
  *   radius[i]     ceil(3 sqrt(lambda_max)), 0 when culled
  *   rect[4i..]    tile rect x_lo, y_lo, x_hi, y_hi (half-open)
  *   tiles[i]      (x_hi-x_lo)*(y_hi-y_lo), 0 when culled
+ *   gflags[i]     with tight != 0 also GF_TIGHT: a tight-box emission
+ *                 decision of the Gaussian lies inside its guard band
  *   rgb[3i..]     max(0, SH colour + 0.5); clamped[3i..] = pre-clamp value < 0
  *   gflags[i]     guard bits (decision within its guard band)
  */
 void orc_preprocess(int64_t n, int sh_degree, const double* means, const double* scales,
                     const double* quats, const double* opac, const double* sh,
-                    const double* cam, int tile_w, int tile_h, const double* guard,
+                    const double* cam, int tile_w, int tile_h, int tight, const double* guard,
                     double* uv, double* depth, uint32_t* depth_bits, double* conic,
                     int32_t* radius, int32_t* rect, int64_t* tiles, double* rgb,
                     uint8_t* clamped, uint8_t* gflags) {
@@ -270,12 +337,23 @@ void orc_preprocess(int64_t n, int sh_degree, const double* means, const double*
         radius[i] = (int32_t)rr;
         rect[4 * i] = x0; rect[4 * i + 1] = y0; rect[4 * i + 2] = x1; rect[4 * i + 3] = y1;
         tiles[i] = area;
+        if (tight) {          /* guard flag of the tight-box emission decisions */
+            int any_guard = 0;
+            for (int tx = x0; tx < x1; ++tx) {
+                int lo, hi, gd = 0;
+                orc_tight_rows(a, b, c, opac[i], u, v, tx * tile_w, tile_w, tile_h, y0, y1,
+                               guard[G_TIGHT_TAU_REL], guard[G_TIGHT_PX], &lo, &hi, &gd);
+                any_guard |= gd;
+            }
+            if (any_guard) gflags[i] |= GF_TIGHT;
+        }
     }
 }
 
 /* ------------------------------------------------------------------ */
 /* Duplicate + sort (Sec. II-A): key = (tile_id << 32) | bits(float depth),
- * emitted in Gaussian order, tiles row-major inside each rect; sorted
+ * emitted in Gaussian order, tiles row-major inside each rect (with tight != 0
+ * only the tiles orc_tight_rows keeps, from uv/conic/opac); sorted
  * ascending by key with ties kept in emission order (stable sort).
  * tile_id = tile_offset + ty*gx + tx. ranges[2t..] = [first, last+1) or (0,0). */
 typedef struct { uint64_t key; int64_t pos; uint32_t val; } orc_kv;
@@ -288,9 +366,11 @@ static int kv_cmp(const void* pa, const void* pb) {
 
 int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_offset,
                  const int32_t* rect, const int64_t* tiles, const uint32_t* depth_bits,
-                 int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+                 int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges,
+                 int tight, int tile_w, int tile_h, const double* uv, const double* conic,
+                 const double* opac) {
     int64_t K = 0;
-    for (int64_t i = 0; i < n; ++i) K += tiles[i];
+    for (int64_t i = 0; i < n; ++i) K += tiles[i];     /* upper bound with tight != 0 */
     if (K > capacity) return -K;
     orc_kv* kv = (orc_kv*)malloc(sizeof(orc_kv) * (size_t)(K > 0 ? K : 1));
     int64_t p = 0;
@@ -298,6 +378,13 @@ int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_of
         if (tiles[i] == 0) continue;
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
             for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
+                if (tight) {          /* drop the tiles the tight box does not reach */
+                    int lo, hi;
+                    int k = orc_tight_rows(conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], opac[i],
+                                           uv[2 * i], uv[2 * i + 1], tx * tile_w, tile_w, tile_h,
+                                           rect[4 * i + 1], rect[4 * i + 3], 0.0, 0.0, &lo, &hi, NULL);
+                    if (k == 0 || ty < lo || ty > hi) continue;
+                }
                 uint64_t tid = (uint64_t)(tile_offset + (int64_t)ty * gx + tx);
                 kv[p].key = (tid << 32) | depth_bits[i];
                 kv[p].val = (uint32_t)i + val_offset;
@@ -305,6 +392,7 @@ int64_t orc_sort(int64_t n, int gx, int gy, int64_t tile_offset, uint32_t val_of
                 ++p;
             }
     }
+    K = p;                    /* instances actually emitted */
     qsort(kv, (size_t)K, sizeof(orc_kv), kv_cmp);
     int64_t nt = (int64_t)gx * gy;
     for (int64_t t = 0; t < 2 * nt; ++t) ranges[t] = 0;
@@ -540,7 +628,7 @@ void orc_backward(int64_t n, int sh_degree, const double* means, const double* s
     double* rgb = (double*)calloc((size_t)n * 3 + 1, sizeof(double));
     uint8_t* clamped = (uint8_t*)calloc((size_t)n * 3 + 1, 1);
     uint8_t* gfl = (uint8_t*)calloc((size_t)n + 1, 1);
-    orc_preprocess(n, sh_degree, means, scales, quats, opac, sh, cam, tile_w, tile_h, guard0, uv,
+    orc_preprocess(n, sh_degree, means, scales, quats, opac, sh, cam, tile_w, tile_h, 0, guard0, uv,
                    depth, dbits, conic, radius, rect, tiles, rgb, clamped, gfl);
     int64_t K = 0;
     for (int64_t i = 0; i < n; ++i) K += tiles[i];
@@ -548,7 +636,8 @@ void orc_backward(int64_t n, int sh_degree, const double* means, const double* s
     uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(K + 1));
     uint32_t* vals = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(K + 1));
     uint32_t* ranges = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * ntile + 2));
-    orc_sort(n, gx, (H + tile_h - 1) / tile_h, 0, 0, rect, tiles, dbits, K, keys, vals, ranges);
+    orc_sort(n, gx, (H + tile_h - 1) / tile_h, 0, 0, rect, tiles, dbits, K, keys, vals, ranges,
+             0, tile_w, tile_h, NULL, NULL, NULL);
 
     /* 2D gradients: du dv da db dc do dr dg db */
     double* G2 = (double*)calloc((size_t)n * 9 + 1, sizeof(double));

@@ -19,6 +19,7 @@ LGS_ERR_CAPACITY = 4
 LGS_ERR_NONFINITE = 5
 LGS_ERR_TIMEOUT = 6
 LGS_ERR_CUDA = 7
+LGS_ERR_INTERNAL = 8
 
 LGS_MAX_VIEWS = 64
 SORT_STATIC_MAX_ENTRIES = 1 << 18
@@ -30,6 +31,7 @@ MODE_LOCALGS = 0
 MODE_PLAIN = 1
 FLAG_COUNT = 1
 FLAG_PERSISTENT = 2
+FLAG_TIGHT = 4
 
 _vp = ctypes.c_void_p
 

@@ -32,16 +32,16 @@ TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
 
 class Renderer:
     def __init__(self, g, cams, tile=(16, 16), mode="localgs", persistent=False, capacity=None,
-                 headroom=1.10, backward=False):
+                 headroom=1.10, backward=False, tight=False):
         self.g, self.cams, self.tile, self.mode = g, cams, tuple(tile), mode
-        flags = L.FLAG_PERSISTENT if persistent else 0
+        flags = (L.FLAG_PERSISTENT if persistent else 0) | (L.FLAG_TIGHT if tight else 0)
         self.cfg = lgs.config(tile, mode, flags)
         self.carr = lgs.cameras(cams)
         dev = g["means"].device
         self.n = g["means"].shape[0]
         self.m = max(self.n * len(cams), 1)
         if capacity is None:
-            probe = lgs.render(g, cams, tile=tile, mode=mode)
+            probe = lgs.render(g, cams, tile=tile, mode=mode, flags=L.FLAG_TIGHT if tight else 0)
             capacity = int(math.ceil(probe["K"] * headroom)) + 1024
             del probe
         self.capacity = capacity
@@ -115,9 +115,10 @@ class Renderer:
         return lgs.split_views(self.rgb, self.cams, 3)
 
 
-def _bucket_key(n, cams, mode, backward):
+def _bucket_key(n, cams, mode, backward, tight=False):
     P = lgs.n_pixels(cams)
-    return f"N2^{int(round(math.log2(max(n, 1))))}|P2^{int(round(math.log2(max(P, 1))))}|V{len(cams)}|{mode}|{'fb' if backward else 'f'}"
+    return (f"N2^{int(round(math.log2(max(n, 1))))}|P2^{int(round(math.log2(max(P, 1))))}|V{len(cams)}|"
+            f"{mode}|{'fb' if backward else 'f'}{'|tight' if tight else ''}")
 
 
 def default_cache_path():
@@ -125,11 +126,11 @@ def default_cache_path():
 
 
 def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persistent=(False, True),
-             reps=10, cache_path=None, use_cache=True):
+             reps=10, cache_path=None, use_cache=True, tight=False):
     """Times every (tile shape, persistent) candidate with graph replays and
     returns {"tile": (w, h), "persistent": bool, "ms": t, "timings": [...]}."""
     cache_path = cache_path or default_cache_path()
-    key = _bucket_key(g["means"].shape[0], cams, mode, backward)
+    key = _bucket_key(g["means"].shape[0], cams, mode, backward, tight)
     cache = {}
     if use_cache and os.path.exists(cache_path):
         try:
@@ -145,7 +146,7 @@ def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persis
         for pers in persistent:
             if pers and mode != "localgs":
                 continue
-            r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward)
+            r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward, tight=tight)
             if backward:
                 r.d_rgb.fill_(1.0 / r.d_rgb.numel())
             r.capture()

@@ -22,6 +22,7 @@ extern "C" const char* lgs_status_string(lgs_status s) {
         case LGS_ERR_NONFINITE: return "non-finite input";
         case LGS_ERR_TIMEOUT: return "bounded device wait gave up";
         case LGS_ERR_CUDA: return "CUDA launch or copy failed";
+        case LGS_ERR_INTERNAL: return "device-side consistency check failed";
         default: return "unknown status";
     }
 }

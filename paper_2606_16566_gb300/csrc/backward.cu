@@ -32,7 +32,6 @@ namespace lgs {
 constexpr int BWD_BATCH = 256;
 constexpr float LOG2E_B = 1.4426950408889634f;
 constexpr float LOG2_ALPHA_MIN_B = -7.9943534368588580f;
-constexpr float LN255_B = 5.5412635451584258f;
 
 struct BwdParams {
     const float4* xy;
@@ -53,39 +52,6 @@ __device__ __forceinline__ float ex2_approx_b(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// Identical to the forward kernel's warp mask (conservative tight box).
-template <int TW, int TH>
-__device__ __forceinline__ uint32_t warp_mask_b(float a, float b, float c, float o, float mux,
-                                                float muy, int X0, int Y0) {
-    constexpr int ROWS = TH / 8;
-    float tau = 2.f * (LN255_B + __logf(o));
-    tau = fmaf(tau, 1.001f, 0.02f);
-    if (!(tau > 0.f)) return 0u;
-    const float det = fmaf(a, c, -b * b);
-    if (!(det > 0.f)) return 0xffu;
-    const float ct = c * tau, at = a * tau;
-    const float xr = sqrtf(ct / det);
-    float x0 = (float)X0 - mux, x1 = (float)(X0 + TW - 1) - mux;
-    if (x1 < -xr || x0 > xr) return 0u;
-    x0 = fmaxf(x0, -xr);
-    x1 = fminf(x1, xr);
-    const float dy = sqrtf(at / det);
-    float ymax, ymin;
-    if (-b * dy < a * x0)      ymax = (-b * x0 + sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
-    else if (-b * dy > a * x1) ymax = (-b * x1 + sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
-    else                       ymax = dy;
-    if (b * dy < a * x0)       ymin = (-b * x0 - sqrtf(fmaxf(0.f, ct - det * x0 * x0))) / c;
-    else if (b * dy > a * x1)  ymin = (-b * x1 - sqrtf(fmaxf(0.f, ct - det * x1 * x1))) / c;
-    else                       ymin = -dy;
-    const float ylo = fmaxf((float)Y0, muy + ymin - 0.015625f);
-    const float yhi = fminf((float)(Y0 + TH - 1), muy + ymax + 0.015625f);
-    if (!(ylo <= yhi)) return 0u;
-    const int ys = (int)ceilf(ylo), ye = (int)floorf(yhi);
-    if (ys > ye) return 0u;
-    const int ws = (ys - Y0) / ROWS, we = (ye - Y0) / ROWS;
-    return ((1u << (we - ws + 1)) - 1u) << ws;
 }
 
 // Sum of v[0..7] over the warp: lane L ends up holding the total of value
@@ -186,8 +152,8 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
                                           fmaf(Fn, LOG2E_B, __log2f(co.w)));
             sDE[threadIdx.x] = make_float2(Dn * LOG2E_B, En * LOG2E_B);
             sC[threadIdx.x] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
-            sM[threadIdx.x] = (uint8_t)warp_mask_b<TW, TH>(co.x, co.y, co.z, co.w, xy.x + xy.z,
-                                                           xy.y + xy.w, X0, Y0);
+            sM[threadIdx.x] = (uint8_t)warp_mask<TW, TH>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
+                                                           __fadd_rn(xy.y, xy.w), X0, Y0);
             sId[threadIdx.x] = id;
 #pragma unroll
             for (int k = 0; k < 9; ++k) sG[threadIdx.x][k] = 0.f;

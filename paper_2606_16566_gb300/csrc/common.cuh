@@ -23,6 +23,7 @@ struct ViewRec {
 struct Views {
     int32_t n;
     int32_t tile_w, tile_h;
+    int32_t flags;       // lgs_config flags
     uint32_t n_tiles;    // total tiles over all views
     uint32_t n_pix;      // total pixels over all views
     ViewRec v[LGS_MAX_VIEWS];
@@ -120,6 +121,129 @@ __device__ __forceinline__ float plain_power(float4 co, float dx, float dy) {
     const float t2 = __fmaf_rn(co.z, __fmul_rn(dy, dy), t1);
     const float t3 = __fmul_rn(co.y, __fmul_rn(dx, dy));
     return __fmaf_rn(-0.5f, t2, -t3);
+}
+
+// ---------------------------------------------------------------- tight box
+// Integer floor division for any sign of p (q > 0).
+__device__ __forceinline__ int floor_div(int p, int q) {
+    return p >= 0 ? p / q : -((-p + q - 1) / q);
+}
+
+constexpr float TIGHT_LN255 = 5.5412635451584258f;  // ln 255
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Per-entry constants of the conservative tight box (Sec. III-C2) of a
+// Gaussian's alpha >= 1/255 region: the ellipse a x~^2 + 2b x~y~ + c y~^2 = tau
+// around the mean (mux, muy), tau = 2 ln(255 o), widened against FP32 rounding
+// to tau' = 1.001 tau + 0.02. kind: 0 = no region (tau' <= 0), 2 = the conic is
+// not positive definite (no box: every row counts), 1 = box.
+struct TightBox {
+    float mux, muy, a, b, ic, det, ct, xr, bdy, dy;
+    int kind;
+};
+
+__device__ __forceinline__ TightBox tight_box(float a, float b, float c, float o, float mux,
+                                              float muy) {
+    TightBox t;
+    float tau = __fmul_rn(2.f, __fadd_rn(TIGHT_LN255, __logf(o)));
+    tau = __fmaf_rn(tau, 1.001f, 0.02f);
+    const float det = __fmaf_rn(a, c, -__fmul_rn(b, b));
+    t.kind = !(tau > 0.f) ? 0 : (!(det > 0.f) ? 2 : 1);
+    const float idet = rcp_approx(det);
+    t.mux = mux;
+    t.muy = muy;
+    t.a = a;
+    t.b = b;
+    t.ic = rcp_approx(c);
+    t.det = det;
+    t.ct = __fmul_rn(c, tau);
+    t.xr = sqrt_approx(__fmul_rn(t.ct, idet));                 // half width of the ellipse
+    t.dy = sqrt_approx(__fmul_rn(__fmul_rn(a, tau), idet));    // half height
+    t.bdy = __fmul_rn(b, t.dy);
+    return t;
+}
+
+// Rows of the tight box over one pixel column strip X0 .. X0+tw-1: the ellipse
+// cut to the strip's x-range, its lowest and highest points over that range
+// from Case A (the root at the strip's left edge), Case B (the right edge) or
+// Case C (the ellipse's own extreme, +-d_y), widened by 1/64 px at both ends.
+// Returns 0 when the strip misses the ellipse, 2 when there is no box, else 1
+// with [*P, *Q] = the integer pixel rows ceil(lower), floor(upper) (clamped
+// to +-2^30; empty when *P > *Q). Every step is an explicitly rounded
+// intrinsic or a single approximate instruction, so every kernel that calls
+// this (preprocess, emission, render, adjoint) gets bit-identical spans. The
+// approximations (relative error ~1e-7) sit far inside the widening margin, so
+// every pixel whose FP32 alpha clears 1/255 lies inside the box.
+__device__ __forceinline__ int column_rows(const TightBox& t, int X0, int tw, int* P, int* Q) {
+    if (t.kind != 1) return t.kind;
+    float x0 = __fsub_rn((float)X0, t.mux), x1 = __fsub_rn((float)(X0 + tw - 1), t.mux);
+    if (x1 < -t.xr || x0 > t.xr) return 0;
+    x0 = fmaxf(x0, -t.xr);
+    x1 = fminf(x1, t.xr);
+    const float ax0 = __fmul_rn(t.a, x0), ax1 = __fmul_rn(t.a, x1);
+    // roots of the ellipse at x: y = (-b x +- sqrt(c tau - det x^2)) / c
+    const float r0 = sqrt_approx(fmaxf(0.f, __fmaf_rn(-t.det, __fmul_rn(x0, x0), t.ct)));
+    const float r1 = sqrt_approx(fmaxf(0.f, __fmaf_rn(-t.det, __fmul_rn(x1, x1), t.ct)));
+    const float bx0 = __fmul_rn(t.b, x0), bx1 = __fmul_rn(t.b, x1);
+    float ymax, ymin;
+    if (-t.bdy < ax0)      ymax = __fmul_rn(__fsub_rn(r0, bx0), t.ic);
+    else if (-t.bdy > ax1) ymax = __fmul_rn(__fsub_rn(r1, bx1), t.ic);
+    else                   ymax = t.dy;
+    if (t.bdy < ax0)       ymin = __fmul_rn(__fsub_rn(-r0, bx0), t.ic);
+    else if (t.bdy > ax1)  ymin = __fmul_rn(__fsub_rn(-r1, bx1), t.ic);
+    else                   ymin = -t.dy;
+    const float lo = __fsub_rn(__fadd_rn(t.muy, ymin), 0.015625f);
+    const float hi = __fadd_rn(__fadd_rn(t.muy, ymax), 0.015625f);
+    *P = (int)ceilf(fminf(fmaxf(lo, -1073741824.f), 1073741824.f));
+    *Q = (int)floorf(fminf(fmaxf(hi, -1073741824.f), 1073741824.f));
+    return 1;
+}
+
+// Tile rows [*lo, *hi] of the rect rows [ry0, ry1) that the tight box of
+// column strip X0 .. X0+tw-1 reaches (tile height th); returns their number.
+__device__ __forceinline__ int tight_tile_rows(const TightBox& t, int X0, int tw, int th, int ry0,
+                                               int ry1, int* lo, int* hi) {
+    int P = 0, Q = 0;
+    const int r = column_rows(t, X0, tw, &P, &Q);
+    int l = ry0, h = ry1 - 1;
+    if (r == 0) return 0;
+    if (r == 1) {
+        if (P > Q) return 0;
+        l = max(l, floor_div(P, th));
+        h = min(h, floor_div(Q, th));
+    }
+    *lo = l;
+    *hi = h;
+    return h >= l ? h - l + 1 : 0;
+}
+
+// Warp-strip mask of one Gaussian for one tile (Sec. III-C2/C3): the rows of
+// the tile that the conservative tight box of the tile's column strip reaches
+// (column_rows), grouped by warp strip. Every pixel whose FP32 alpha clears
+// 1/255 lies in a set strip.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_mask(float a, float b, float c, float o, float mux,
+                                              float muy, int X0, int Y0) {
+    constexpr int ROWS = TH / 8;
+    int P = 0, Q = 0;
+    const int r = column_rows(tight_box(a, b, c, o, mux, muy), X0, TW, &P, &Q);
+    if (r == 0) return 0u;
+    if (r == 2) return 0xffu;
+    const int ys = max(Y0, P), ye = min(Y0 + TH - 1, Q);
+    if (ys > ye) return 0u;
+    const int ws = (ys - Y0) / ROWS, we = (ye - Y0) / ROWS;
+    return ((1u << (we - ws + 1)) - 1u) << ws;
 }
 
 }  // namespace lgs

@@ -26,6 +26,7 @@ inline lgs_status make_views(const lgs_camera* cams, int32_t n_views, const lgs_
     vs->n = n_views;
     vs->tile_w = cfg->tile_w;
     vs->tile_h = cfg->tile_h;
+    vs->flags = cfg->flags;
     uint64_t toff = 0, poff = 0;
     for (int v = 0; v < n_views; ++v) {
         const lgs_camera& c = cams[v];

@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreParams p, Views vs) 
                 if (col.y < 0.f) { col.y = 0.f; fl |= 2; }
                 if (col.z < 0.f) { col.z = 0.f; fl |= 4; }
                 const float inv_det = 1.f / det;
+                const float ca = S11 * inv_det, cb = -d01 * inv_det, cc = S00 * inv_det;
                 reinterpret_cast<float4*>(p.xy)[m] = make_float4(u.hi, vv.hi, u.lo, vv.lo);
-                reinterpret_cast<float4*>(p.conic)[m] =
-                    make_float4(S11 * inv_det, -d01 * inv_det, S00 * inv_det, op);
+                reinterpret_cast<float4*>(p.conic)[m] = make_float4(ca, cb, cc, op);
                 reinterpret_cast<float4*>(p.rgb)[m] = make_float4(col.x, col.y, col.z, zf);
                 rad = (int32_t)rr;
                 ntiles = area;

@@ -1,28 +1,29 @@
-// sort.cu -- stage 2 of the 3DGS pipeline (Local-GS Sec. II-A): a parallel
-// prefix scan over tiles-touched, duplication of every visible Gaussian into
-// one 64-bit key (tile_id << 32 | depth bits) per tile of its rect, a stable
-// LSD radix sort of the (key, value) pairs, and per-tile ranges.
+// sort.cu -- stage 2 of the 3DGS pipeline (Local-GS Sec. II-A): duplication of
+// every visible (view, Gaussian) entry into one instance per tile it touches,
+// ordering of the instances by the 64-bit key (tile_id << 32 | depth bits)
+// with ties kept in emission order, and per-tile ranges.
 //
 // The instance count K is only known on the device. Every kernel reads it from
 // the caller's status words, so the whole stage is enqueued without a host
 // round trip (and is capturable in a CUDA graph); grids are sized for the
 // caller's capacity and blocks past K exit at once.
 //
-// The sort is a most-significant-digit-first radix sort of the 64-bit keys
-// whose first "digit" is the whole tile id:
-//  1. emission writes (tile id, value) pairs in emission order;
-//  2. stable LSD passes of 8 bits over the ceil(log2(tiles)) tile bits only
-//     (reduce-then-scan: upsweep digit histograms per 4096-pair block, a scan
-//     of each digit row, and a downsweep that ranks pairs stably inside the
-//     block with __match_any_sync and per-warp counters, reorders them in
-//     shared memory and writes runs of equal digits contiguously);
-//  3. per-tile ranges from the tile-sorted ids;
-//  4. a stable LSD sort of each tile's segment by the 32 depth bits, in
-//     shared memory (segments of up to 2048 instances, one CTA each) or
-//     chunk-wise through global scratch (larger segments).
-// Step 2 keeps emission order inside every tile and step 4 is stable, so the
-// result is bit for bit the stable sort of (tile << 32 | depth) keys, with four
-// fewer passes over global memory than sorting the whole 64-bit key.
+// Depth first, tiles second:
+//  1. a stable LSD radix sort of the M entries by their 32 depth bits (culled
+//     entries carry an all-ones key and sort last);
+//  2. an exclusive scan of tiles-touched in that order gives every entry its
+//     instance offset and K (with LGS_FLAG_TIGHT the counts are those of the
+//     tight box, computed here: count_tight);
+//  3. emission writes (tile id, entry) pairs entry by entry in depth order;
+//  4. stable LSD passes over the ceil(log2(tiles)) tile-id bits only;
+//  5. per-tile ranges from the sorted tile ids.
+// Inside a tile the instances keep their emission order, which is (depth,
+// entry index), so the result is bit for bit the stable sort of the 64-bit
+// keys -- with 4 passes over the M entries instead of 4 passes over the K > M
+// instances for the depth bits.
+// Every radix pass is one "onesweep" kernel: per 4096-element block a stable
+// in-shared-memory ranking and a decoupled look-back over the earlier blocks'
+// digit counts (see onesweep_pass).
 #include "common.cuh"
 #include "host.h"
 
@@ -207,6 +208,187 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
             tkey[start + e] = otoff + (oy0 + ry) * ogx + ox0 + rx;
             tval[start + e] = oent;
         }
+    }
+}
+
+// ------------------------------------------------------------------ tight-box emission
+// With LGS_FLAG_TIGHT an entry emits only the tiles of its rect that its tight
+// box (TightBox / tight_tile_rows) reaches: column strip by column strip, tile
+// rows ascending inside a column. Counting (count_tight) and emission
+// (emit_pairs_tight) walk the same column items with the same function, so the
+// counts the scan turns into offsets are exactly the instances emitted.
+//
+// Both kernels give each warp 32 consecutive entries of the depth order; each
+// lane loads its entry's rect and box, the entries expand into column items
+// (one per rect column), and the lanes take 32 items at a time, each finding
+// its owner entry by a binary search over the warp's inclusive column counts,
+// so wide and narrow Gaussians share the work evenly.
+struct TightLane {
+    uint32_t x0, y0, y1, wd, toff, gx, ent;
+    TightBox tb;
+};
+
+__device__ __forceinline__ TightLane tight_lane_load(uint32_t ent, bool live, const uint64_t* rect,
+                                                     const float4* xy, const float4* conic,
+                                                     const Views& vs, int64_t n) {
+    TightLane L{};
+    L.gx = 1;
+    L.ent = ent;
+    if (live) {
+        const uint64_t r = rect[ent];
+        L.x0 = (uint32_t)(r & 0xffff);
+        L.y0 = (uint32_t)((r >> 16) & 0xffff);
+        L.wd = (uint32_t)((r >> 32) & 0xffff) - L.x0;
+        L.y1 = (uint32_t)((r >> 48) & 0xffff);
+        const ViewRec& cv = vs.v[(int)(ent / (uint64_t)n)];
+        L.toff = cv.tile_off;
+        L.gx = (uint32_t)cv.gx;
+        const float4 co = conic[ent];
+        const float4 p = xy[ent];
+        L.tb = tight_box(co.x, co.y, co.z, co.w, __fadd_rn(p.x, p.z), __fadd_rn(p.y, p.w));
+    }
+    return L;
+}
+
+// The tight box of lane `own`'s entry, broadcast to the calling lane.
+__device__ __forceinline__ TightBox tight_box_of(const TightBox& tb, int own) {
+    TightBox o;
+    o.mux = __shfl_sync(0xffffffffu, tb.mux, own);
+    o.muy = __shfl_sync(0xffffffffu, tb.muy, own);
+    o.a = __shfl_sync(0xffffffffu, tb.a, own);
+    o.b = __shfl_sync(0xffffffffu, tb.b, own);
+    o.ic = __shfl_sync(0xffffffffu, tb.ic, own);
+    o.det = __shfl_sync(0xffffffffu, tb.det, own);
+    o.ct = __shfl_sync(0xffffffffu, tb.ct, own);
+    o.xr = __shfl_sync(0xffffffffu, tb.xr, own);
+    o.bdy = __shfl_sync(0xffffffffu, tb.bdy, own);
+    o.dy = __shfl_sync(0xffffffffu, tb.dy, own);
+    o.kind = __shfl_sync(0xffffffffu, tb.kind, own);
+    return o;
+}
+
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// first lane whose inclusive count exceeds e
+__device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t e) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+        if (v <= e) lo += step;
+    }
+    return lo;
+}
+
+// Tight instance count of every entry in depth order: tiles_sorted[j] =
+// instances that emission will write for entry order[j] (0 for culled entries).
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) count_tight(const uint32_t* order, const uint32_t* tiles,
+                                                   const uint64_t* rect, const float4* xy,
+                                                   const float4* conic, int64_t m, int64_t n, Views vs,
+                                                   uint32_t* tiles_sorted) {
+    __shared__ uint32_t cnt[256];
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t wbase = idx - (threadIdx.x & 31);
+    if (wbase >= m) return;
+    const int lane = threadIdx.x & 31;
+    const int wofs = threadIdx.x & ~31;
+    const bool valid = idx < m;
+    const uint32_t ent = valid ? order[idx] : 0u;
+    const bool live = valid && tiles[ent] != 0u;
+    const TightLane L = tight_lane_load(ent, live, rect, xy, conic, vs, n);
+    cnt[threadIdx.x] = 0u;
+    __syncwarp();
+    const uint32_t iw = warp_inclusive_sum(L.wd);
+    const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
+    const uint32_t ew = iw - L.wd;
+    for (uint32_t e0 = 0; e0 < items; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const int own = owner_lane(iw, e);
+        const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
+        const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
+        const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
+        const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
+        const TightBox ot = tight_box_of(L.tb, own);
+        if (e < items) {
+            int rlo, rhi;
+            const int k = tight_tile_rows(ot, (int)(ox0 + col) * TW, TW, TH, oy0, oy1, &rlo, &rhi);
+            if (k) atomicAdd(&cnt[wofs + own], (uint32_t)k);
+        }
+    }
+    __syncwarp();
+    if (valid) tiles_sorted[idx] = cnt[threadIdx.x];
+}
+
+// Emission of the tight instances: entry e's instances fill exactly
+// [offsets[e], offsets[e] + tiles_sorted[e]); a warp lays the runs of its column
+// items out one after the other from its first offset (warp scan of the run
+// lengths). Should the recount ever differ from count_tight's (it cannot: same
+// function, same inputs), the warp writes only inside its own range, pads it
+// with tile 0 / entry 0 and records LGS_ERR_INTERNAL.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, const uint32_t* tiles_sorted,
+                                                        const uint32_t* offsets, const uint64_t* rect,
+                                                        const float4* xy, const float4* conic,
+                                                        int64_t m, int64_t n, int64_t* status,
+                                                        int64_t capacity, Views vs, uint32_t* tkey,
+                                                        uint32_t* tval) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t wbase = idx - (threadIdx.x & 31);
+    if (wbase >= m) return;
+    if (status[LGS_ST_NUM_INSTANCES] > capacity) return;
+    const int lane = threadIdx.x & 31;
+    const bool valid = idx < m;
+    const uint32_t cnt = valid ? tiles_sorted[idx] : 0u;
+    const uint32_t incl = warp_inclusive_sum(cnt);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
+    const TightLane L = tight_lane_load(cnt ? order[idx] : 0u, cnt != 0u, rect, xy, conic, vs, n);
+    const uint32_t iw = warp_inclusive_sum(L.wd);
+    const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
+    const uint32_t ew = iw - L.wd;
+    uint32_t run = 0;
+    for (uint32_t e0 = 0; e0 < items; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const int own = owner_lane(iw, e);
+        const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
+        const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
+        const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
+        const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
+        const uint32_t otoff = __shfl_sync(0xffffffffu, L.toff, own);
+        const uint32_t ogx = __shfl_sync(0xffffffffu, L.gx, own);
+        const uint32_t oent = __shfl_sync(0xffffffffu, L.ent, own);
+        const TightBox ot = tight_box_of(L.tb, own);
+        const uint32_t tx = ox0 + col;
+        int rlo = 0, rhi = -1;
+        uint32_t k = 0;
+        if (e < items) k = (uint32_t)tight_tile_rows(ot, (int)tx * TW, TW, TH, oy0, oy1, &rlo, &rhi);
+        const uint32_t ik = warp_inclusive_sum(k);
+        const uint32_t pos = run + ik - k;
+        for (uint32_t r = 0; r < k; ++r) {
+            const uint32_t q = pos + r;
+            if (q < total) {
+                tkey[start + q] = otoff + ((uint32_t)rlo + r) * ogx + tx;
+                tval[start + q] = oent;
+            }
+        }
+        run += __shfl_sync(0xffffffffu, ik, 31);
+    }
+    if (run != total) {
+        for (uint32_t q = run + lane; q < total; q += 32) {
+            tkey[start + q] = 0u;
+            tval[start + q] = 0u;
+        }
+        if (lane == 0) report_error(status, LGS_ERR_INTERNAL, (int64_t)total - (int64_t)run);
     }
 }
 
@@ -567,8 +749,19 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
         t = v0; v0 = v1; v1 = t;
     }
     const uint32_t* order = v0;
-    // 2. scan of tiles-touched in depth order
-    gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->tiles_s);
+    // 2. scan of tiles-touched (with LGS_FLAG_TIGHT: of the tight counts) in depth order
+    const bool tight = (vs->flags & LGS_FLAG_TIGHT) != 0;
+    const float4* pxy = reinterpret_cast<const float4*>(pre->xy);
+    const float4* pco = reinterpret_cast<const float4*>(pre->conic);
+    const unsigned eg = (unsigned)ceil_div(m, 256);
+    if (!tight)
+        gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->tiles_s);
+    else if (vs->tile_w == 16)
+        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
+    else if (vs->tile_w == 8)
+        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
+    else
+        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
@@ -578,8 +771,20 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     const int passes = tile_passes(vs->n_tiles);
     uint32_t *ka = ws->ak, *kb = ws->bk;
     uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
-    emit_pairs<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect,
-                                                          m, n, d_status, capacity, *vs, ka, va);
+    if (tight) {
+        if (vs->tile_w == 16)
+            emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+                                                        m, n, d_status, capacity, *vs, ka, va);
+        else if (vs->tile_w == 8)
+            emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+                                                       m, n, d_status, capacity, *vs, ka, va);
+        else
+            emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+                                                       m, n, d_status, capacity, *vs, ka, va);
+    } else {
+        emit_pairs<<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, m, n, d_status,
+                                      capacity, *vs, ka, va);
+    }
     // 4. tile-id passes over the K instances
     if (passes > 0) onesweep_prepare(ka, d_status, capacity, passes, ws->bases + OS_MAX_DIGITS * RADIX, s);
     for (int p = 0; p < passes; ++p) {
@@ -605,6 +810,9 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
     lgs_status st = make_views(cams, n_views, cfg, &vs);
     if (st != LGS_OK) return st;
     if (!pre->tiles || !pre->rect || !pre->depth) return LGS_ERR_ARG;
+    if ((cfg->flags & LGS_FLAG_TIGHT) && (!pre->xy || !pre->conic)) return LGS_ERR_ARG;
+    if ((cfg->flags & LGS_FLAG_TIGHT) && (!aligned16(pre->xy) || !aligned16(pre->conic)))
+        return LGS_ERR_ALIGN;
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
         (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;
@@ -664,6 +872,9 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
     if (m > LGS_SORT_STATIC_MAX_ENTRIES || capacity > LGS_SORT_STATIC_MAX_INSTANCES)
         return LGS_ERR_UNSUPPORTED;
     if (!pre->tiles || !pre->rect || !pre->depth) return LGS_ERR_ARG;
+    if ((cfg->flags & LGS_FLAG_TIGHT) && (!pre->xy || !pre->conic)) return LGS_ERR_ARG;
+    if ((cfg->flags & LGS_FLAG_TIGHT) && (!aligned16(pre->xy) || !aligned16(pre->conic)))
+        return LGS_ERR_ALIGN;
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
         (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;

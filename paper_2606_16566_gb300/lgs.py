@@ -217,16 +217,16 @@ def render_bwd(g, cams, cfg, pre: PreOut, vals, ranges, final_T, n_contrib, dL_d
 class RenderFunction(torch.autograd.Function):
     """Differentiable forward render of a batch of views.
 
-    forward(means, scales, quats, opacities, sh, cams, tile) -> (rgb, final_T), both
-    flat over the views (see include/lgs.h); backward runs lgs_render_bwd from the
-    saved preprocess outputs, tile lists, final_T and n_contrib.
+    forward(means, scales, quats, opacities, sh, cams, tile, flags) -> (rgb, final_T),
+    both flat over the views (see include/lgs.h); backward runs lgs_render_bwd
+    from the saved preprocess outputs, tile lists, final_T and n_contrib.
     """
 
     @staticmethod
-    def forward(ctx, means, scales, quats, opacities, sh, cams, tile=(16, 16)):
+    def forward(ctx, means, scales, quats, opacities, sh, cams, tile=(16, 16), flags=0):
         g = {"means": means.contiguous(), "scales": scales.contiguous(), "quats": quats.contiguous(),
              "opacities": opacities.contiguous(), "sh": sh.contiguous()}
-        res = render(g, cams, tile=tile)
+        res = render(g, cams, tile=tile, flags=flags)
         ctx.cams, ctx.cfg, ctx.g = cams, res["cfg"], g
         ctx.pre = res["pre"]
         ctx.save_for_backward(res["vals"], res["ranges"], res["T_flat"], res["nc_flat"])
@@ -237,7 +237,7 @@ class RenderFunction(torch.autograd.Function):
         vals, ranges, T, nc = ctx.saved_tensors
         gr = render_bwd(ctx.g, ctx.cams, ctx.cfg, ctx.pre, vals, ranges, T, nc, d_rgb.contiguous(),
                         None if d_T is None else d_T.contiguous())
-        return gr["means"], gr["scales"], gr["quats"], gr["opacities"], gr["sh"], None, None
+        return gr["means"], gr["scales"], gr["quats"], gr["opacities"], gr["sh"], None, None, None
 
 
 def read_status(status, stream=None) -> np.ndarray:

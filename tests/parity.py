@@ -134,7 +134,7 @@ def assert_image_parity(rep, what=""):
     assert rep["n_guard"] <= max(2, GUARD_FRAC * rep["n_pix"]), (what, rep)
 
 
-def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None, tile_mask=None):
+def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None, tile_mask=None, tight=False):
     """One view of a GPU render (host copies) against the oracle.
 
     A pixel "disagrees" when its contributor count differs (compared by the
@@ -146,7 +146,8 @@ def full_view_parity(scene, cam, res_gpu_view, tile, oracle_res=None, tile_mask=
     alpha >= 1/255 there. Disagreeing pixels are the guard items; the image
     tolerance applies to all others."""
     tw, th = tile
-    o = oracle_res if oracle_res is not None else oracle.render(scene, cam, tw, th, tile_mask=tile_mask)
+    o = oracle_res if oracle_res is not None else oracle.render(scene, cam, tw, th, tile_mask=tile_mask,
+                                                                tight=tight)
     W, H = cam["width"], cam["height"]
     g_vals, g_ranges = res_gpu_view["vals"], res_gpu_view["ranges"]
     bad = list_mismatch_tiles(g_vals, g_ranges, o["vals"], o["ranges"])
