@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="only run warm-up + steps of the Local-GS pipeline (for ncu), no report")
     p.add_argument("--views", type=int, default=8, help="views of the outdoor workload (profiling)")
-    p.add_argument("--mode", default="localgs", choices=["localgs", "plain"])
+    p.add_argument("--mode", default="localgs", choices=["localgs", "plain", "literal", "global"])
     p.add_argument("--no-batched", action="store_true", help="skip the 64-view batched workload")
     p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
     p.add_argument("--tight", action="store_true", help="with --profile: tight-box emission")
@@ -320,7 +320,10 @@ def run_ours(args, rank, world):
         return
     TF = L.FLAG_TIGHT
     variants = {"localgs": lgs.config(tile, "localgs"), "plain": lgs.config(tile, "plain"),
-                "localgs_tight": lgs.config(tile, "localgs", TF), "plain_tight": lgs.config(tile, "plain", TF)}
+                "localgs_tight": lgs.config(tile, "localgs", TF), "plain_tight": lgs.config(tile, "plain", TF),
+                "literal_tight": lgs.config(tile, "literal", TF)}
+    forward_only = {"literal_tight"}       # the paper-literal study variant has no adjoint
+    mode_of = {L.MODE_LOCALGS: "localgs", L.MODE_PLAIN: "plain", L.MODE_LITERAL: "literal"}
 
     # discover K and size the instance buffers once (outside the timed region)
     probe = lgs.render(g, cams, tile=tile)
@@ -330,8 +333,7 @@ def run_ours(args, rank, world):
     # schedule work of the Local-GS render (pixel-Gaussian pairs) and K, counted once
     counts = {}
     for name, cfg in variants.items():
-        pipe.step(lgs.config(tile, "plain" if name.startswith("plain") else "localgs",
-                             cfg.flags | L.FLAG_COUNT))
+        pipe.step(lgs.config(tile, mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT))
         st = lgs.read_status(pipe.status)
         if st[L.ST_CODE] != 0:
             raise L.LgsError(int(st[L.ST_CODE]), f"device status in {name}")
@@ -340,9 +342,10 @@ def run_ours(args, rank, world):
 
     pipe.setup_backward()
     for _ in range(args.warmup):
-        for cfg in variants.values():
+        for name, cfg in variants.items():
             pipe.step(cfg)
-            pipe.stage_backward(cfg)
+            if name not in forward_only:
+                pipe.stage_backward(cfg)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -351,7 +354,8 @@ def run_ours(args, rank, world):
     with Clocks(dev.index) as clk:
         for name, cfg in variants.items():
             fwd[name] = time_steps(pipe, cfg, args.steps, flush)
-            fb[name] = time_steps(pipe, cfg, n_bw, flush, backward=True)
+            if name not in forward_only:
+                fb[name] = time_steps(pipe, cfg, n_bw, flush, backward=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -359,14 +363,14 @@ def run_ours(args, rank, world):
     if st[L.ST_CODE] != 0:
         raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
     ms = {n: float(fwd[n].sum(1).mean()) for n in variants}
-    ms_b = {n: float(fb[n].sum(1).mean()) for n in variants}
+    ms_b = {n: float(fb[n].sum(1).mean()) for n in fb}
     if world > 1:
-        names = list(variants)
-        t = torch.tensor([ms[n] for n in names] + [ms_b[n] for n in names], device=dev)
+        names, names_b = list(ms), list(ms_b)
+        t = torch.tensor([ms[n] for n in names] + [ms_b[n] for n in names_b], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         vals = t.tolist()
         ms = dict(zip(names, vals[:len(names)]))
-        ms_b = dict(zip(names, vals[len(names):]))
+        ms_b = dict(zip(names_b, vals[len(names):]))
     views = len(cams)
     P = lgs.n_pixels(cams)
     # headline: the faster of the two Local-GS emissions (both reported)
@@ -383,14 +387,17 @@ def run_ours(args, rank, world):
     cfg_l = variants[head]
 
     def summary(name):
-        f, b = fwd[name].mean(0), fb[name].mean(0)
-        return {"frames_s": world * views / (ms[name] * 1e-3), "mpix_s": world * P / 1e6 / (ms[name] * 1e-3),
-                "ms_per_step": ms[name],
-                "stage_ms": {"preprocess": float(f[0]), "sort": float(f[1]), "render": float(f[2])},
-                "fwd_bwd": {"frames_s": world * views / (ms_b[name] * 1e-3),
-                            "mpix_s": world * P / 1e6 / (ms_b[name] * 1e-3), "ms_per_step": ms_b[name],
-                            "backward_ms": float(b[3])},
-                "instances_K": counts[name]["K"], "pairs": counts[name]["pairs"]}
+        f = fwd[name].mean(0)
+        out = {"frames_s": world * views / (ms[name] * 1e-3), "mpix_s": world * P / 1e6 / (ms[name] * 1e-3),
+               "ms_per_step": ms[name],
+               "stage_ms": {"preprocess": float(f[0]), "sort": float(f[1]), "render": float(f[2])},
+               "instances_K": counts[name]["K"], "pairs": counts[name]["pairs"]}
+        if name in fb:
+            b = fb[name].mean(0)
+            out["fwd_bwd"] = {"frames_s": world * views / (ms_b[name] * 1e-3),
+                              "mpix_s": world * P / 1e6 / (ms_b[name] * 1e-3), "ms_per_step": ms_b[name],
+                              "backward_ms": float(b[3])}
+        return out
 
     # end to end: host scene -> device, pipeline, image -> host, every step
     e2e = None
@@ -450,7 +457,7 @@ def run_ours(args, rank, world):
                      "traffic": recorded_traffic("render_localgs_16x16_" + emission),
                      "work": f"{counts[head]['pairs']} pixel-Gaussian pairs x 19 FP32 flops",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)"},
-        "gpu_launches": len(variants) * (pipe.launches() * (args.steps + n_bw) + 2 * n_bw),
+        "gpu_launches": len(variants) * pipe.launches() * args.steps + len(fb) * (pipe.launches() + 2) * n_bw,
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched": batched,

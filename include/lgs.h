@@ -106,6 +106,19 @@ typedef struct {
 
 #define LGS_MODE_LOCALGS 0      /* hoisting + warp culling + warp-coherent blending */
 #define LGS_MODE_PLAIN 1        /* per-pixel global-coordinate loop with per-pixel branches */
+/* Forward-only study variants of the Local-GS kernel (lgs_render_bwd and
+ * LGS_FLAG_PERSISTENT reject them):
+ * LGS_MODE_LITERAL: Alg. 1 right column read literally -- no per-pixel 1/255
+ *   test (the warp mask is the only culling) and no per-pixel stop: every
+ *   Gaussian whose warp bit is set blends with w = alpha T, C += f w, T -= w,
+ *   until all 32 pixels of the warp have T < 1e-4 (checked before each
+ *   Gaussian). n_contrib = position of the last Gaussian the warp processed.
+ * LGS_MODE_GLOBAL: the contract of LGS_MODE_LOCALGS with the hoisted
+ *   coefficients expressed in global pixel coordinates (origin at pixel 0,0)
+ *   instead of the tile frame: the "w/o local coordinates" configuration of
+ *   Sec. III-B4 / Table V, whose FP32 cancellation grows with the image size. */
+#define LGS_MODE_LITERAL 2
+#define LGS_MODE_GLOBAL 3
 
 #define LGS_FLAG_COUNT 1        /* render also counts its schedule's pixel-Gaussian pairs into d_status[LGS_ST_PAIRS] */
 #define LGS_FLAG_PERSISTENT 2   /* render with persistent CTAs pulling tiles from a work queue */

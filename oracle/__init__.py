@@ -68,6 +68,8 @@ def lib():
         L.orc_blend.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                 _u32p, _u32p, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
                                 _dp, _dp, _u32p, _u8p, _u32p, _u32p, _u8p]
+        L.orc_blend_literal.argtypes = [ctypes.c_int] * 5 + [_dp, _u32p, _u32p, ctypes.c_int64,
+                                                             _dp, _dp, _dp, _dp, _dp, _dp, _dp, _u32p, _u8p]
         L.orc_hoist.argtypes = [ctypes.c_double] * 6 + [_dp]
         L.orc_warp_mask.restype = ctypes.c_uint32
         L.orc_warp_mask.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int] * 5
@@ -184,14 +186,35 @@ def blend(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, til
             "stop_pos": stop_pos, "n_useful": n_useful}
 
 
+def blend_literal(pre, vals, ranges, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, n_warps=8):
+    """Paper-literal warp-coherent blending (no per-pixel stop or 1/255 test)."""
+    L = lib()
+    W, H = cam["width"], cam["height"]
+    bg = np.asarray(cam["bg"], np.float64)
+    out_rgb = np.zeros((3, H, W))
+    final_T = np.zeros((H, W))
+    n_contrib = np.zeros((H, W), np.uint32)
+    pguard = np.zeros((H, W), np.uint8)
+    v = np.ascontiguousarray(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    g = np.ascontiguousarray(guard, dtype=np.float64)
+    L.orc_blend_literal(W, H, tile_w, tile_h, n_warps, _p(bg, _dp), _p(v, _u32p), _p(ranges, _u32p), 0,
+                        _p(pre["uv"], _dp), _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
+                        _p(pre["rgb"], _dp), _p(g, _dp), _p(out_rgb, _dp), _p(final_T, _dp),
+                        _p(n_contrib, _u32p), _p(pguard, _u8p))
+    return {"rgb": out_rgb, "final_T": final_T, "n_contrib": n_contrib, "pguard": pguard}
+
+
 def render(scene, cam, tile_w=16, tile_h=16, guard=DEFAULT_GUARD, exact=False, tile_mask=None,
-           tight=False):
+           tight=False, literal=False):
     """Full forward pass for one view: preprocess, sort, blend (optionally only
     the pixels of the tiles selected by tile_mask; tight-box emission with
-    tight=True)."""
+    tight=True; the paper-literal blending with literal=True)."""
     pre = preprocess(scene, cam, tile_w, tile_h, guard, exact, tight)
     keys, vals, ranges = sort(pre, cam, tile_w, tile_h)
-    img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard, tile_mask)
+    if literal:
+        img = blend_literal(pre, vals, ranges, cam, tile_w, tile_h, guard)
+    else:
+        img = blend(pre, vals, ranges, cam, tile_w, tile_h, guard, tile_mask)
     img.update({"pre": pre, "keys": keys, "vals": vals, "ranges": ranges})
     return img
 
@@ -275,7 +298,7 @@ def ewa(cam, t, Sig):
     return out
 
 
-__all__ = ["render", "backward", "preprocess", "sort", "blend", "hoist", "warp_mask", "tight_rows",
+__all__ = ["render", "backward", "preprocess", "sort", "blend", "blend_literal", "hoist", "warp_mask", "tight_rows",
            "localgs_pairs",
            "sh_basis", "quat_to_rot", "cov3d", "ewa", "num_threads", "cam_array",
            "DEFAULT_GUARD"]

@@ -31,6 +31,9 @@
  *   orc_blend        pinned (closed form, two-Gaussian composition, alpha
  *                    stack stop rule, invariants, brute force without tiling)
  *   orc_hoist        pinned (identity with the direct quadratic form)
+ *   orc_blend_literal pinned (equals orc_blend where no pixel has a sub-1/255
+ *                    alpha inside its warp's box and no pixel stops; T stays
+ *                    the product of (1 - alpha); brute force per strip)
  *   orc_warp_mask    pinned (brute-force sampling of the ellipse)
  *   orc_tight_rows   pinned (brute-force alpha over every pixel of the rect:
  *                    no dropped tile holds a pixel with alpha >= 1/255; every
@@ -460,6 +463,75 @@ void orc_blend(int W, int H, int tile_w, int tile_h, const double* bg,
         pguard[pix] = g;
         if (stop_pos) stop_pos[pix] = stop;
         if (n_useful) n_useful[pix] = useful;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Paper-literal warp-coherent blending (Alg. 1 right column read literally,
+ * Sec. III-D). Per tile and per warp strip (n_warps strips of tile_w x
+ * tile_h/n_warps pixels), the tile list in order. A Gaussian is processed by
+ * the strip iff the strip's pixel rows meet the tight box of the tile column
+ * (orc_tight_rows at pixel-row granularity: the widened rule of the
+ * emission). Before each processed Gaussian the strip leaves the list when
+ * every pixel of it inside the image has T < 1e-4. A processed Gaussian blends
+ * into every pixel of the strip, with no 1/255 test:
+ *   alpha = min(0.99, o e^p), w = alpha T, C += f w, T -= w.
+ * n_contrib = list position (1-based) of the last processed Gaussian.
+ * pguard[pix] = 1 when a decision of the pixel's strip (a mask bit or the
+ * exit test on the strip's largest T) lies inside its guard band. */
+void orc_blend_literal(int W, int H, int tile_w, int tile_h, int n_warps, const double* bg,
+                       const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
+                       const double* uv, const double* conic, const double* opac,
+                       const double* rgb, const double* guard, double* out_rgb, double* final_T,
+                       uint32_t* n_contrib, uint8_t* pguard) {
+    int gx = (W + tile_w - 1) / tile_w, gy = (H + tile_h - 1) / tile_h;
+    int rows = tile_h / n_warps;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t ts = 0; ts < (int64_t)gx * gy * n_warps; ++ts) {
+        int64_t tile = ts / n_warps;
+        int w = (int)(ts % n_warps);
+        int tx = (int)(tile % gx), ty = (int)(tile / gx);
+        int X0 = tx * tile_w, Y0 = ty * tile_h + w * rows;
+        int pxs[64], pys[64], np = 0;
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < tile_w; ++c)
+                if (X0 + c < W && Y0 + r < H) { pxs[np] = X0 + c; pys[np] = Y0 + r; ++np; }
+        if (np == 0) continue;
+        double T[64], C[64][3];
+        for (int q = 0; q < np; ++q) { T[q] = 1.0; C[q][0] = C[q][1] = C[q][2] = 0.0; }
+        uint32_t s = ranges[2 * (tile_offset + tile)], e = ranges[2 * (tile_offset + tile) + 1];
+        uint32_t last = 0;
+        uint8_t g = 0;
+        for (uint32_t k = s; k < e; ++k) {
+            uint32_t id = vals[k];
+            double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2], o = opac[id];
+            int lo, hi, gd = 0;
+            int hit = orc_tight_rows(a, b, c, o, uv[2 * id], uv[2 * id + 1], X0, tile_w, 1, Y0, Y0 + rows,
+                                     guard[G_TIGHT_TAU_REL], guard[G_TIGHT_PX], &lo, &hi, &gd);
+            if (gd) g = 1;
+            if (hit == 0) continue;
+            double tmax = 0.0;
+            for (int q = 0; q < np; ++q) if (T[q] > tmax) tmax = T[q];
+            if (fabs(tmax - 1e-4) < guard[G_STOP_REL] * 1e-4) g = 1;
+            if (tmax < 1e-4) break;                     /* the whole strip is done */
+            for (int q = 0; q < np; ++q) {
+                double dx = uv[2 * id] - pxs[q], dy = uv[2 * id + 1] - pys[q];
+                double p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+                double al = o * exp(p);
+                if (al > 0.99) al = 0.99;
+                double wgt = al * T[q];
+                for (int ch = 0; ch < 3; ++ch) C[q][ch] += rgb[3 * id + ch] * wgt;
+                T[q] -= wgt;
+            }
+            last = k - s + 1;
+        }
+        for (int q = 0; q < np; ++q) {
+            int64_t pix = (int64_t)pys[q] * W + pxs[q];
+            for (int ch = 0; ch < 3; ++ch) out_rgb[(int64_t)ch * W * H + pix] = C[q][ch] + T[q] * bg[ch];
+            final_T[pix] = T[q];
+            n_contrib[pix] = last;
+            pguard[pix] = g;
+        }
     }
 }
 

@@ -29,6 +29,8 @@ ST_CODE, ST_DETAIL, ST_NUM_INSTANCES, ST_NONFINITE, ST_PAIRS, ST_QUEUE, ST_QUEUE
 
 MODE_LOCALGS = 0
 MODE_PLAIN = 1
+MODE_LITERAL = 2
+MODE_GLOBAL = 3
 FLAG_COUNT = 1
 FLAG_PERSISTENT = 2
 FLAG_TIGHT = 4

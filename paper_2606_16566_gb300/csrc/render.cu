@@ -104,7 +104,20 @@ struct LocalSmem {
     uint8_t sM[BATCH];  // warp-strip mask
 };
 
-template <int TW, int TH, bool COUNT>
+// Variants of the Local-GS tile loop:
+//  VAR_CONTRACT: the per-pixel definition (1/255 skip and stop as predicates),
+//                hoisted in the tile-centred frame;
+//  VAR_LITERAL:  Alg. 1 right column read literally (Sec. III-D): no per-pixel
+//                1/255 test (the warp mask is the only culling), w = alpha T,
+//                C += f w, T -= w, and the warp leaves its list once every
+//                lane has T < 1e-4 (checked before each Gaussian);
+//  VAR_GLOBAL:   the contract evaluated with the hoist in global pixel
+//                coordinates (origin at pixel (0, 0)): the "w/o local coord"
+//                configuration of Sec. III-B4 / Table V, kept for the FP32
+//                precision study.
+constexpr int VAR_CONTRACT = 0, VAR_LITERAL = 1, VAR_GLOBAL = 2;
+
+template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT>
 __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t tile,
                                              LocalSmem& S) {
     float4* sV = S.sV;
@@ -113,8 +126,11 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     uint8_t* sM = S.sM;
     const TileCtx t = tile_ctx<TW, TH>(vs, p, tile);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float Ox = (float)t.X0 + 0.5f * (TW - 1), Oy = (float)t.Y0 + 0.5f * (TH - 1);
-    const float xl = (float)t.lx - 0.5f * (TW - 1), yl = (float)t.ly - 0.5f * (TH - 1);
+    const bool global_frame = VAR == VAR_GLOBAL;
+    const float Ox = global_frame ? 0.f : (float)t.X0 + 0.5f * (TW - 1);
+    const float Oy = global_frame ? 0.f : (float)t.Y0 + 0.5f * (TH - 1);
+    const float xl = global_frame ? (float)t.px : (float)t.lx - 0.5f * (TW - 1);
+    const float yl = global_frame ? (float)t.py : (float)t.ly - 0.5f * (TH - 1);
     const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
 
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
@@ -152,7 +168,10 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 while (bits) {
                     const int k = __ffs(bits) - 1;
                     bits &= bits - 1;
-                    if (COUNT) {
+                    if (VAR == VAR_LITERAL) {
+                        if (__all_sync(0xffffffffu, !t.inside || T < 1e-4f)) { bits = 0; done = true; break; }
+                        if (COUNT) ++pairs;
+                    } else if (COUNT) {
                         if (__all_sync(0xffffffffu, done)) { bits = 0; break; }
                         ++pairs;
                     }
@@ -163,6 +182,15 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                     const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
                                      fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
                     const float al = fminf(0.99f, ex2_approx(pw));
+                    if (VAR == VAR_LITERAL) {
+                        const float w = al * T;
+                        C0 = fmaf(col.x, w, C0);
+                        C1 = fmaf(col.y, w, C1);
+                        C2 = fmaf(col.z, w, C2);
+                        T = T - w;
+                        last = b0 + (uint32_t)g + 1u;
+                        continue;
+                    }
                     const bool valid = !done && pw >= LOG2_ALPHA_MIN;
                     const float tT = fmaf(-al, T, T);
                     const bool stop = valid && tT < 1e-4f;
@@ -187,10 +215,10 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
 }
 
 // One CTA per tile.
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT>
 __global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
     __shared__ LocalSmem S;
-    localgs_tile<TW, TH, COUNT>(p, vs, blockIdx.x, S);
+    localgs_tile<TW, TH, COUNT, VAR>(p, vs, blockIdx.x, S);
 }
 
 // Persistent CTAs: each pulls the next tile index from a work-queue counter
@@ -271,7 +299,7 @@ lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, bool 
     if (mode == LGS_MODE_PLAIN) {
         if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_plain<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
-    } else if (persistent) {
+    } else if (persistent && mode == LGS_MODE_LOCALGS) {
         if (cudaMemsetAsync(p.status + LGS_ST_QUEUE, 0, sizeof(int64_t), s) != cudaSuccess)
             return LGS_ERR_CUDA;
         int dev = 0, sms = 0, per_sm = 0;
@@ -286,6 +314,12 @@ lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, bool 
             const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
             render_localgs_persistent<TW, TH, false><<<g, block, 0, s>>>(p, vs);
         }
+    } else if (mode == LGS_MODE_LITERAL) {
+        if (count) render_localgs<TW, TH, true, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
+        else       render_localgs<TW, TH, false, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
+    } else if (mode == LGS_MODE_GLOBAL) {
+        if (count) render_localgs<TW, TH, true, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
+        else       render_localgs<TW, TH, false, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
     } else {
         if (count) render_localgs<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_localgs<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
@@ -308,7 +342,8 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     if (st != LGS_OK) return st;
     st = check_pre(pre);
     if (st != LGS_OK) return st;
-    if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
+    if (cfg->mode < LGS_MODE_LOCALGS || cfg->mode > LGS_MODE_GLOBAL) return LGS_ERR_UNSUPPORTED;
+    if ((cfg->flags & LGS_FLAG_PERSISTENT) && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
     RenderParams p;
     p.xy = reinterpret_cast<const float4*>(pre->xy);

@@ -30,7 +30,8 @@ def _stream(stream=None):
 def config(tile=(16, 16), mode="localgs", flags=0, batch=0) -> L.lgs_config:
     if tuple(tile) not in _TILES:
         raise ValueError(f"tile shape {tile} not in {_TILES}")
-    m = {"localgs": L.MODE_LOCALGS, "plain": L.MODE_PLAIN}[mode]
+    m = {"localgs": L.MODE_LOCALGS, "plain": L.MODE_PLAIN, "literal": L.MODE_LITERAL,
+         "global": L.MODE_GLOBAL}[mode]
     return L.lgs_config(int(tile[0]), int(tile[1]), m, int(batch), int(flags))
 
 
