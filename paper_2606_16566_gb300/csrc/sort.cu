@@ -9,8 +9,9 @@
 // caller's capacity and blocks past K exit at once.
 //
 // Depth first, tiles second:
-//  1. a stable LSD radix sort of the M entries by their 32 depth bits (culled
-//     entries carry an all-ones key and sort last);
+//  1. a stable LSD radix sort of the visible entries by their 32 depth bits
+//     (the first pass reads tiles-touched and depth directly and drops the
+//     culled entries);
 //  2. an exclusive scan of tiles-touched in that order gives every entry its
 //     instance offset and K (with LGS_FLAG_TIGHT the counts are those of the
 //     tight box, computed here: count_tight);
@@ -19,7 +20,7 @@
 //  5. per-tile ranges from the sorted tile ids.
 // Inside a tile the instances keep their emission order, which is (depth,
 // entry index), so the result is bit for bit the stable sort of the 64-bit
-// keys -- with 4 passes over the M entries instead of 4 passes over the K > M
+// keys -- with 4 passes over the (visible) entries instead of 4 passes over the K
 // instances for the depth bits.
 // Every radix pass is one "onesweep" kernel: per 4096-element block a stable
 // in-shared-memory ranking and a decoupled look-back over the earlier blocks'
@@ -36,6 +37,7 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 2048
 
 constexpr int RADIX = 256;
+constexpr int OS_MAX_DIGITS_E = 4;   // digit positions an emission histogram can hold
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -71,6 +73,19 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     uint32_t excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0u);
     __syncthreads();
     return excl;
+}
+
+// ------------------------------------------------------------------ element counts
+// Element count of a pass: the device word *cnt (0 when it exceeds the host
+// bound n, e.g. K beyond the capacity) when cnt is given, else n.
+__device__ __forceinline__ int64_t pass_count(const int64_t* cnt, int64_t n) {
+    if (!cnt) return n;
+    const int64_t k = *cnt;
+    return k > n ? 0 : k;
+}
+
+__device__ __forceinline__ int64_t sort_count(const int64_t* status, int64_t capacity) {
+    return pass_count(status + LGS_ST_NUM_INSTANCES, capacity);
 }
 
 // ------------------------------------------------------------------ scan of tiles
@@ -156,14 +171,16 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
                                                   const uint32_t* offsets, const uint64_t* rect,
                                                   int64_t m, int64_t n, const int64_t* status,
                                                   int64_t capacity, Views vs, uint32_t* tkey,
-                                                  uint32_t* tval) {
+                                                  uint32_t* tval, int npass, uint32_t* ghist) {
+    __shared__ uint32_t h[OS_MAX_DIGITS_E * RADIX];
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
-    if (wbase >= m) return;                                  // whole warp past the end
-    if (status[LGS_ST_NUM_INSTANCES] > capacity) return;
     const int lane = threadIdx.x & 31;
     const bool valid = idx < m;
-    const uint32_t cnt = valid ? tiles[idx] : 0u;
+    const bool fits = status[LGS_ST_NUM_INSTANCES] <= capacity;
+    const uint32_t cnt = (valid && fits) ? tiles[idx] : 0u;
     const uint32_t ent = cnt ? order[idx] : 0u;
     uint32_t incl = cnt;
 #pragma unroll
@@ -172,43 +189,49 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
         if (lane >= o) incl += y;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
-    // per-entry data the owners hand out
-    uint32_t x0 = 0, y0 = 0, wd = 1, toff = 0, gx = 1;
-    if (cnt) {
-        const uint64_t r = rect[ent];
-        x0 = (uint32_t)(r & 0xffff);
-        y0 = (uint32_t)((r >> 16) & 0xffff);
-        wd = (uint32_t)((r >> 32) & 0xffff) - x0;
-        const ViewRec& c = vs.v[(int)(ent / (uint64_t)n)];
-        toff = c.tile_off;
-        gx = (uint32_t)c.gx;
-    }
-    const uint32_t excl = incl - cnt;
-    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        // owner = first lane with incl > e
-        int lo = 0;
+    if (wbase < m && total > 0) {
+        const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
+        // per-entry data the owners hand out
+        uint32_t x0 = 0, y0 = 0, wd = 1, toff = 0, gx = 1;
+        if (cnt) {
+            const uint64_t r = rect[ent];
+            x0 = (uint32_t)(r & 0xffff);
+            y0 = (uint32_t)((r >> 16) & 0xffff);
+            wd = (uint32_t)((r >> 32) & 0xffff) - x0;
+            const ViewRec& c = vs.v[(int)(ent / (uint64_t)n)];
+            toff = c.tile_off;
+            gx = (uint32_t)c.gx;
+        }
+        const uint32_t excl = incl - cnt;
+        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            // owner = first lane with incl > e
+            int lo = 0;
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-            if (v <= e) lo += step;
-        }
-        const int own = lo;
-        const uint32_t k = e - __shfl_sync(0xffffffffu, excl, own);
-        const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, own);
-        const uint32_t oy0 = __shfl_sync(0xffffffffu, y0, own);
-        const uint32_t ow = __shfl_sync(0xffffffffu, wd, own);
-        const uint32_t otoff = __shfl_sync(0xffffffffu, toff, own);
-        const uint32_t ogx = __shfl_sync(0xffffffffu, gx, own);
-        const uint32_t oent = __shfl_sync(0xffffffffu, ent, own);
-        if (e < total) {
-            const uint32_t ry = k / ow, rx = k - ry * ow;
-            tkey[start + e] = otoff + (oy0 + ry) * ogx + ox0 + rx;
-            tval[start + e] = oent;
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (v <= e) lo += step;
+            }
+            const int own = lo;
+            const uint32_t k = e - __shfl_sync(0xffffffffu, excl, own);
+            const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, own);
+            const uint32_t oy0 = __shfl_sync(0xffffffffu, y0, own);
+            const uint32_t ow = __shfl_sync(0xffffffffu, wd, own);
+            const uint32_t otoff = __shfl_sync(0xffffffffu, toff, own);
+            const uint32_t ogx = __shfl_sync(0xffffffffu, gx, own);
+            const uint32_t oent = __shfl_sync(0xffffffffu, ent, own);
+            if (e < total) {
+                const uint32_t ry = k / ow, rx = k - ry * ow;
+                const uint32_t tile = otoff + (oy0 + ry) * ogx + ox0 + rx;
+                tkey[start + e] = tile;
+                tval[start + e] = oent;
+                for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX + ((tile >> (8 * p)) & 0xffu)], 1u);
+            }
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
 // ------------------------------------------------------------------ tight-box emission
@@ -289,12 +312,13 @@ __device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t e) {
 }
 
 // Tight instance count of every entry in depth order: tiles_sorted[j] =
-// instances that emission will write for entry order[j] (0 for culled entries).
+// instances that emission will write for entry order[j] (0 past the visible
+// entries).
 template <int TW, int TH>
 __global__ void __launch_bounds__(256) count_tight(const uint32_t* order, const uint32_t* tiles,
                                                    const uint64_t* rect, const float4* xy,
-                                                   const float4* conic, int64_t m, int64_t n, Views vs,
-                                                   uint32_t* tiles_sorted) {
+                                                   const float4* conic, int64_t m, const int64_t* mv,
+                                                   int64_t n, Views vs, uint32_t* tiles_sorted) {
     __shared__ uint32_t cnt[256];
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
@@ -302,8 +326,9 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order, const 
     const int lane = threadIdx.x & 31;
     const int wofs = threadIdx.x & ~31;
     const bool valid = idx < m;
-    const uint32_t ent = valid ? order[idx] : 0u;
-    const bool live = valid && tiles[ent] != 0u;
+    const bool visible = idx < pass_count(mv, m);
+    const uint32_t ent = visible ? order[idx] : 0u;
+    const bool live = visible && tiles[ent] != 0u;
     const TightLane L = tight_lane_load(ent, live, rect, xy, conic, vs, n);
     cnt[threadIdx.x] = 0u;
     __syncwarp();
@@ -340,83 +365,88 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
                                                         const float4* xy, const float4* conic,
                                                         int64_t m, int64_t n, int64_t* status,
                                                         int64_t capacity, Views vs, uint32_t* tkey,
-                                                        uint32_t* tval) {
+                                                        uint32_t* tval, int npass, uint32_t* ghist) {
+    __shared__ uint32_t h[OS_MAX_DIGITS_E * RADIX];
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
-    if (wbase >= m) return;
-    if (status[LGS_ST_NUM_INSTANCES] > capacity) return;
     const int lane = threadIdx.x & 31;
     const bool valid = idx < m;
-    const uint32_t cnt = valid ? tiles_sorted[idx] : 0u;
+    const bool fits = status[LGS_ST_NUM_INSTANCES] <= capacity;
+    const uint32_t cnt = (valid && fits) ? tiles_sorted[idx] : 0u;
     const uint32_t incl = warp_inclusive_sum(cnt);
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
-    const TightLane L = tight_lane_load(cnt ? order[idx] : 0u, cnt != 0u, rect, xy, conic, vs, n);
-    const uint32_t iw = warp_inclusive_sum(L.wd);
-    const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
-    const uint32_t ew = iw - L.wd;
-    uint32_t run = 0;
-    for (uint32_t e0 = 0; e0 < items; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        const int own = owner_lane(iw, e);
-        const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
-        const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
-        const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
-        const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
-        const uint32_t otoff = __shfl_sync(0xffffffffu, L.toff, own);
-        const uint32_t ogx = __shfl_sync(0xffffffffu, L.gx, own);
-        const uint32_t oent = __shfl_sync(0xffffffffu, L.ent, own);
-        const TightBox ot = tight_box_of(L.tb, own);
-        const uint32_t tx = ox0 + col;
-        int rlo = 0, rhi = -1;
-        uint32_t k = 0;
-        if (e < items) k = (uint32_t)tight_tile_rows(ot, (int)tx * TW, TW, TH, oy0, oy1, &rlo, &rhi);
-        const uint32_t ik = warp_inclusive_sum(k);
-        const uint32_t pos = run + ik - k;
-        for (uint32_t r = 0; r < k; ++r) {
-            const uint32_t q = pos + r;
-            if (q < total) {
-                tkey[start + q] = otoff + ((uint32_t)rlo + r) * ogx + tx;
-                tval[start + q] = oent;
+    if (wbase < m && total > 0) {
+        const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
+        const TightLane L = tight_lane_load(cnt ? order[idx] : 0u, cnt != 0u, rect, xy, conic, vs, n);
+        const uint32_t iw = warp_inclusive_sum(L.wd);
+        const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
+        const uint32_t ew = iw - L.wd;
+        uint32_t run = 0;
+        for (uint32_t e0 = 0; e0 < items; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            const int own = owner_lane(iw, e);
+            const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
+            const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
+            const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
+            const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
+            const uint32_t otoff = __shfl_sync(0xffffffffu, L.toff, own);
+            const uint32_t ogx = __shfl_sync(0xffffffffu, L.gx, own);
+            const uint32_t oent = __shfl_sync(0xffffffffu, L.ent, own);
+            const TightBox ot = tight_box_of(L.tb, own);
+            const uint32_t tx = ox0 + col;
+            int rlo = 0, rhi = -1;
+            uint32_t k = 0;
+            if (e < items) k = (uint32_t)tight_tile_rows(ot, (int)tx * TW, TW, TH, oy0, oy1, &rlo, &rhi);
+            const uint32_t ik = warp_inclusive_sum(k);
+            const uint32_t pos = run + ik - k;
+            for (uint32_t r = 0; r < k; ++r) {
+                const uint32_t q = pos + r;
+                if (q < total) {
+                    const uint32_t tile = otoff + ((uint32_t)rlo + r) * ogx + tx;
+                    tkey[start + q] = tile;
+                    tval[start + q] = oent;
+                    for (int p = 0; p < npass; ++p)
+                        atomicAdd(&h[p * RADIX + ((tile >> (8 * p)) & 0xffu)], 1u);
+                }
             }
+            run += __shfl_sync(0xffffffffu, ik, 31);
         }
-        run += __shfl_sync(0xffffffffu, ik, 31);
-    }
-    if (run != total) {
-        for (uint32_t q = run + lane; q < total; q += 32) {
-            tkey[start + q] = 0u;
-            tval[start + q] = 0u;
+        if (run != total) {
+            for (uint32_t q = run + lane; q < total; q += 32) {
+                tkey[start + q] = 0u;
+                tval[start + q] = 0u;
+                for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX], 1u);
+            }
+            if (lane == 0) report_error(status, LGS_ERR_INTERNAL, (int64_t)total - (int64_t)run);
         }
-        if (lane == 0) report_error(status, LGS_ERR_INTERNAL, (int64_t)total - (int64_t)run);
     }
-}
-
-// ------------------------------------------------------------------ stable ranking
-__device__ __forceinline__ int64_t sort_count(const int64_t* status, int64_t capacity) {
-    int64_t K = status[LGS_ST_NUM_INSTANCES];
-    return K > capacity ? 0 : K;
-}
-
-// Element count of a radix pass: the device instance count (checked against
-// the capacity) when `status` is given, else the host-known count.
-__device__ __forceinline__ int64_t pass_count(const int64_t* status, int64_t n) {
-    return status ? sort_count(status, n) : n;
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
 // ------------------------------------------------------------------ radix passes (onesweep)
 // A stable LSD pass moves (u32 key, u32 value) pairs by one 8-bit digit in a
 // single kernel. Each block takes the next tile index in launch order
-// (atomic counter), ranks its 4096 keys stably in shared memory, publishes its
-// per-digit counts, and obtains the count of every digit in all earlier tiles
-// by looking back over their published words (decoupled look-back, Merrill &
-// Garland): a word carries either the tile's own count (AGG) or its inclusive
-// prefix (PRE); the walk stops at the first PRE. A block only waits on tiles
-// that were handed out before its own and therefore are already running.
-// Every wait is bounded: after OS_SPIN_LIMIT polls the block records
+// (atomic counter), counts its 4096 keys' digits in shared memory and
+// publishes those counts at once, obtains the count of every digit in all
+// earlier tiles by looking back over their published words (decoupled
+// look-back, Merrill & Garland): a word carries either the tile's own count
+// (AGG) or its inclusive prefix (PRE); the walk stops at the first PRE. Only
+// then does it rank its keys stably and scatter them. A block only waits on
+// tiles that were handed out before its own and therefore are already
+// running; every wait is bounded: after OS_SPIN_LIMIT polls the block records
 // LGS_ERR_TIMEOUT and continues. The digit bases of all passes come from one
 // histogram kernel over the input keys (digits of later passes are counted on
 // the same keys, since a pass only permutes them).
+//
+// The first pass over the entries reads no key array: it forms each entry's
+// key (the bits of its depth, which order like the positive floats they are)
+// and value (the entry index) from tiles-touched and depth, and drops culled
+// entries (no tile) altogether, so later passes and stages see only the
+// visible entries; their number goes to a device word.
 constexpr int OS_THREADS = 256;
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;   // 4096
@@ -425,23 +455,57 @@ constexpr uint64_t OS_PRE = 2ull << 62;
 constexpr uint64_t OS_VAL = (1ull << 62) - 1;
 constexpr int OS_SPIN_LIMIT = 1 << 20;
 constexpr int OS_MAX_DIGITS = 4;
+static_assert(OS_MAX_DIGITS == OS_MAX_DIGITS_E, "emission histograms cover every tile-id digit");
 
-// Per-digit-position histograms of the keys: ghist[p*256 + d] += count of
-// elements whose digit p (bits 8p..8p+7) is d, for p < npass.
-__global__ void __launch_bounds__(256) onesweep_histogram(const uint32_t* keys, const int64_t* status,
-                                                          int64_t count, int npass, uint32_t* ghist) {
+// Where a pass reads its pairs: key/value arrays, or (k == nullptr) the
+// entries' tiles-touched and depth.
+struct OsSrc {
+    const uint32_t* k;
+    const uint32_t* v;
+    const uint32_t* tiles;
+    const float* depth;
+};
+
+__device__ __forceinline__ bool os_load(const OsSrc& src, int64_t i, uint32_t& k, uint32_t& v) {
+    if (src.k) {
+        k = src.k[i];
+        v = src.v[i];
+        return true;
+    }
+    v = (uint32_t)i;
+    if (src.tiles[i] == 0u) {
+        k = 0xffffffffu;
+        return false;
+    }
+    k = __float_as_uint(src.depth[i]);
+    return true;
+}
+
+// Per-digit-position histograms of the (kept) keys: ghist[p*256 + d] += count
+// of kept elements whose digit p (bits 8p..8p+7) is d, for p < npass; with a
+// synthesized source also the number of kept elements into *kept.
+__global__ void __launch_bounds__(256) onesweep_histogram(OsSrc src, const int64_t* cnt, int64_t count,
+                                                          int npass, uint32_t* ghist, int64_t* kept) {
     __shared__ uint32_t h[OS_MAX_DIGITS * RADIX];
+    __shared__ uint32_t s_kept;
     for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
+    if (threadIdx.x == 0) s_kept = 0;
     __syncthreads();
-    const int64_t K = pass_count(status, count);
+    const int64_t K = pass_count(cnt, count);
+    uint32_t my_kept = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
+        uint32_t k, v;
+        if (!os_load(src, i, k, v)) continue;
+        ++my_kept;
         for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX + ((k >> (8 * p)) & 0xffu)], 1u);
     }
+    if (kept && my_kept) atomicAdd(&s_kept, my_kept);
     __syncthreads();
     for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
         if (h[i]) atomicAdd(&ghist[i], h[i]);
+    if (kept && threadIdx.x == 0 && s_kept)
+        atomicAdd(reinterpret_cast<unsigned long long*>(kept), (unsigned long long)s_kept);
 }
 
 // In place: each digit position's 256 counts -> exclusive prefix (one block per position).
@@ -456,7 +520,7 @@ __global__ void __launch_bounds__(RADIX) onesweep_bases(uint32_t* ghist) {
 struct OneSmem {
     uint32_t cnt[OS_THREADS / 32][RADIX];   // per-warp digit counters -> (digit, warp) offsets
     uint32_t ws[32];
-    uint32_t start[RADIX];   // block-local start of each digit
+    uint32_t start[RADIX];   // digit counts of the tile, then block-local start of each digit
     uint32_t base[RADIX];    // global output position of each digit's first element in this tile
     uint32_t tile;
     uint32_t keys[OS_TILE];
@@ -464,14 +528,14 @@ struct OneSmem {
 };
 
 // Keys are ranked warp by warp: warp w owns tile elements [w*512, (w+1)*512),
-// taken 32 at a time in order; __match_any_sync groups equal digits and the
+// taken 32 at a time in order; per-bit ballots group equal digits and the
 // warp's private counters give each key its rank among equal digits of the
 // warp's range, with no block barrier. A digit-major exclusive scan over
 // (digit, warp) then gives each (digit, warp) pair its place in the tile.
-__global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const int64_t* count_status, int64_t count, int shift,
-    const uint32_t* bases, unsigned long long* look, uint32_t* tile_counter, int64_t* err_status) {
+__global__ void __launch_bounds__(OS_THREADS, 3) onesweep_pass(
+    OsSrc src, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* cnt,
+    int64_t count, int shift, const uint32_t* bases, unsigned long long* look, uint32_t* tile_counter,
+    int64_t* err_status) {
     constexpr int NW = OS_THREADS / 32;
     constexpr int PER_WARP = OS_TILE / NW;      // 512
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -480,45 +544,29 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
     const uint32_t lt = lanemask_lt();
     if (t == 0) S.tile = atomicAdd(tile_counter, 1u);
     for (int d = lane; d < RADIX; d += 32) S.cnt[warp][d] = 0;
+    S.start[t] = 0;
     __syncthreads();
     const uint32_t tile = S.tile;
-    const int64_t K = pass_count(count_status, count);
+    const int64_t K = pass_count(cnt, count);
     const int64_t first = (int64_t)tile * OS_TILE;
     if (first >= K) return;
     const int n_valid = (int)min((int64_t)OS_TILE, K - first);
     uint32_t k[OS_ITEMS], v[OS_ITEMS];
-    uint16_t rk[OS_ITEMS];
+    uint32_t keep = 0;      // bit i: item i is a kept element
     const int wbase = warp * PER_WARP;
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
         const int j = wbase + i * 32 + lane;
-        const bool ok = j < n_valid;
-        k[i] = ok ? kin[first + j] : 0xffffffffu;
-        v[i] = ok ? vin[first + j] : 0u;
+        k[i] = 0xffffffffu;
+        v[i] = 0u;
+        if (j < n_valid && os_load(src, first + j, k[i], v[i])) keep |= 1u << i;
     }
+    // early digit counts of the tile, published before ranking
 #pragma unroll
-    for (int i = 0; i < OS_ITEMS; ++i) {
-        const int j = wbase + i * 32 + lane;
-        const uint32_t d = j < n_valid ? ((k[i] >> shift) & 0xffu) : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const int leader = __ffs(peers) - 1;
-        uint32_t b = 0;
-        if (d < 0x100u && lane == leader) b = S.cnt[warp][d];
-        b = __shfl_sync(0xffffffffu, b, leader);
-        rk[i] = (uint16_t)(b + __popc(peers & lt));
-        __syncwarp();
-        if (d < 0x100u && lane == leader) S.cnt[warp][d] = b + __popc(peers);
-        __syncwarp();
-    }
+    for (int i = 0; i < OS_ITEMS; ++i)
+        if (keep & (1u << i)) atomicAdd(&S.start[(k[i] >> shift) & 0xffu], 1u);
     __syncthreads();
-    // digit totals and per-(digit, warp) prefixes
-    uint32_t pre[NW], total = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        pre[w] = total;
-        total += S.cnt[w][t];
-    }
-    // publish this tile's counts, then look back for the prefix of earlier tiles
+    const uint32_t total = S.start[t];
     unsigned long long* my = look + (int64_t)tile * RADIX + t;
     atomicExch(my, (unsigned long long)((tile == 0 ? OS_PRE : OS_AGG) | total));
     uint64_t prefix = 0;
@@ -541,8 +589,36 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
         }
         atomicExch(my, (unsigned long long)(OS_PRE | (prefix + total)));
     }
-    uint32_t all;
-    const uint32_t st = block_exclusive_scan<OS_THREADS>(total, S.ws, all);
+    // stable rank of every kept key among equal digits of its warp's range; the
+    // lanes holding the same digit (9 bits: 0x100 marks no key) are found with
+    // one ballot per bit
+    uint16_t rk[OS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const uint32_t d = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
+        // every lane of a group reads the group's counter; the group's last
+        // lane advances it
+        const uint32_t b = d < 0x100u ? S.cnt[warp][d] : 0u;
+        rk[i] = (uint16_t)(b + __popc(peers & lt));
+        __syncwarp();
+        if (d < 0x100u && (peers >> lane) == 1u) S.cnt[warp][d] = b + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t pre[NW], acc = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        pre[w] = acc;
+        acc += S.cnt[w][t];
+    }
+    uint32_t n_kept;
+    const uint32_t st = block_exclusive_scan<OS_THREADS>(total, S.ws, n_kept);
     S.start[t] = st;
     S.base[t] = bases[t] + (uint32_t)prefix;
 #pragma unroll
@@ -550,15 +626,14 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
-        const int j = wbase + i * 32 + lane;
-        if (j < n_valid) {
+        if (keep & (1u << i)) {
             const uint32_t pos = S.cnt[warp][(k[i] >> shift) & 0xffu] + rk[i];
             S.keys[pos] = k[i];
             S.vals[pos] = v[i];
         }
     }
     __syncthreads();
-    for (int j = t; j < n_valid; j += OS_THREADS) {
+    for (int j = t; j < (int)n_kept; j += OS_THREADS) {
         const uint32_t key = S.keys[j];
         const uint32_t d = (key >> shift) & 0xffu;
         const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
@@ -568,36 +643,43 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_pass(
 }
 
 // ------------------------------------------------------------------ ranges
-__global__ void tile_ranges(const uint32_t* tkey, const int64_t* status, int64_t capacity,
-                            uint2* ranges) {
+// Per-tile [start, end) of the sorted tile ids; each thread takes 4
+// consecutive instances (one 16-B load when all 4 lie below K).
+__global__ void __launch_bounds__(256) tile_ranges(const uint32_t* tkey, const int64_t* status,
+                                                   int64_t capacity, uint2* ranges) {
     const int64_t K = sort_count(status, capacity);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t tile = tkey[i];
-        if (i == 0 || tkey[i - 1] != tile) ranges[tile].x = (uint32_t)i;
-        if (i == K - 1 || tkey[i + 1] != tile) ranges[tile].y = (uint32_t)(i + 1);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * q < K;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = 4 * q;
+        uint32_t t[4];
+        if (i0 + 3 < K) {
+            const uint4 v = reinterpret_cast<const uint4*>(tkey)[q];
+            t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) t[r] = i0 + r < K ? tkey[i0 + r] : 0u;
+        }
+        uint32_t prev = i0 > 0 ? tkey[i0 - 1] : 0xffffffffu;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t i = i0 + r;
+            if (i >= K) break;
+            if (i == 0 || prev != t[r]) ranges[t[r]].x = (uint32_t)i;
+            const uint32_t next = r < 3 ? (i + 1 < K ? t[r + 1] : 0xffffffffu)
+                                        : (i + 1 < K ? tkey[i + 1] : 0xffffffffu);
+            if (i == K - 1 || next != t[r]) ranges[t[r]].y = (uint32_t)(i + 1);
+            prev = t[r];
+        }
     }
 }
 
-// ------------------------------------------------------------------ depth order of the entries
-// key = depth bits for entries that touch at least one tile (positive floats
-// order like their bit patterns), all-ones for culled entries (sorted last);
-// value = entry index v*N + i.
-__global__ void depth_keys(const uint32_t* tiles, const float* depth, int64_t m, uint32_t* key,
-                           uint32_t* val) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        key[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
-        val[i] = (uint32_t)i;
-    }
-}
-
-// tiles-touched of the entries in depth order
+// tiles-touched of the visible entries in depth order (0 past the mv visible ones)
 __global__ void gather_tiles(const uint32_t* order, const uint32_t* tiles, int64_t m,
-                             uint32_t* tiles_sorted) {
+                             const int64_t* mv, uint32_t* tiles_sorted) {
+    const int64_t nv = pass_count(mv, m);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
          j += (int64_t)gridDim.x * blockDim.x)
-        tiles_sorted[j] = tiles[order[j]];
+        tiles_sorted[j] = j < nv ? tiles[order[j]] : 0u;
 }
 
 // Optional 64-bit keys of the sorted instances: (tile << 32) | bits(depth).
@@ -622,7 +704,8 @@ struct SortWs {
     uint32_t* bk;          // [capacity]
     uint32_t* bv;          // [capacity] values (the caller's vals buffer is the other one)
     unsigned long long* look;  // [256 * max tiles of a pass] look-back words
-    uint32_t* counters;    // [8]: tile counter of the running pass
+    uint32_t* counters;    // tile counter of the running pass (u32 at byte 0 of a 256-B block)
+    int64_t* mvis;         // visible entries (int64 at byte 64 of the same block)
     uint32_t* bases;       // [2 * OS_MAX_DIGITS * 256]: digit bases (entry sort, tile sort)
 };
 
@@ -677,6 +760,7 @@ inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws
         ws->bv = reinterpret_cast<uint32_t*>(p4);
         ws->look = reinterpret_cast<unsigned long long*>(p6);
         ws->counters = reinterpret_cast<uint32_t*>(p7);
+        ws->mvis = reinterpret_cast<int64_t*>(p7 + 64);
         ws->bases = reinterpret_cast<uint32_t*>(p8);
     }
     return off;
@@ -688,26 +772,28 @@ inline int tile_passes(uint32_t n_tiles) {
     return bits == 0 ? 0 : (bits + 7) / 8;
 }
 
-// Digit bases of `npass` LSD passes over `keys` (count from the device when
-// `status` is given): histogram + exclusive scan into bases[npass * 256].
-static void onesweep_prepare(const uint32_t* keys, const int64_t* status, int64_t count, int npass,
-                             uint32_t* bases, cudaStream_t s) {
+// Digit bases of `npass` LSD passes over the pairs of `src` (count from the
+// device word `cnt` when given): histogram + exclusive scan into
+// bases[npass * 256]; with `kept`, also the number of kept elements.
+static void onesweep_prepare(const OsSrc& src, const int64_t* cnt, int64_t count, int npass,
+                             uint32_t* bases, int64_t* kept, cudaStream_t s) {
     cudaMemsetAsync(bases, 0, sizeof(uint32_t) * RADIX * npass, s);
-    onesweep_histogram<<<152 * 4, 256, 0, s>>>(keys, status, count, npass, bases);
+    if (kept) cudaMemsetAsync(kept, 0, sizeof(int64_t), s);
+    onesweep_histogram<<<152 * 4, 256, 0, s>>>(src, cnt, count, npass, bases, kept);
     onesweep_bases<<<npass, RADIX, 0, s>>>(bases);
 }
 
-// One stable LSD pass over u32 keys carrying u32 values (count from the device
-// instance count when `status` is given, else `count`).
-static void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-                       const int64_t* status, int64_t count, int shift, const uint32_t* bases,
-                       const SortWs* ws, int64_t* d_status, cudaStream_t s) {
+// One stable LSD pass over u32 keys carrying u32 values (element count from
+// the device word `cnt` when given, else `count`; the grid covers `count`).
+static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const int64_t* cnt,
+                       int64_t count, int shift, const uint32_t* bases, const SortWs* ws,
+                       int64_t* d_status, cudaStream_t s) {
     const int64_t nt = ceil_div(count, OS_TILE);
     if (nt == 0) return;
     cudaMemsetAsync(ws->look, 0, sizeof(unsigned long long) * RADIX * (size_t)nt, s);
     cudaMemsetAsync(ws->counters, 0, sizeof(uint32_t), s);
     onesweep_pass<<<(unsigned)nt, OS_THREADS, sizeof(OneSmem), s>>>(
-        kin, vin, kout, vout, status, count, shift, bases, ws->look, ws->counters, d_status);
+        src, kout, vout, cnt, count, shift, bases, ws->look, ws->counters, d_status);
 }
 
 }  // namespace lgs
@@ -720,7 +806,8 @@ extern "C" size_t lgs_sort_workspace_size(int64_t m, int64_t capacity) {
 }
 
 // Enqueues the full stage given a workspace layout (shared by the entry points):
-//  1. stable LSD sort of the m entries by depth (culled entries last),
+//  1. stable LSD sort of the visible entries by depth (the first pass drops
+//     the culled ones),
 //  2. scan of tiles-touched in that order -> instance offsets and K,
 //  3. emission of (tile id, entry) pairs in that order,
 //  4. stable LSD passes over the tile-id bits,
@@ -739,12 +826,15 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     }
     cudaFuncSetAttribute(onesweep_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(OneSmem));
-    // 1. entries by depth
-    depth_keys<<<152 * 8, 256, 0, s>>>(pre->tiles, pre->depth, m, ws->ek, ws->ev);
-    onesweep_prepare(ws->ek, nullptr, m, 4, ws->bases, s);
-    uint32_t *k0 = ws->ek, *v0 = ws->ev, *k1 = ws->ek2, *v1 = ws->ev2;
-    for (int shift = 0; shift < 32; shift += 8) {
-        radix_pass(k0, v0, k1, v1, nullptr, m, shift, ws->bases + RADIX * (shift / 8), ws, d_status, s);
+    // 1. visible entries by depth: the first pass forms (depth bits, entry)
+    //    from tiles-touched and depth and drops the culled entries
+    const OsSrc entries{nullptr, nullptr, pre->tiles, pre->depth};
+    onesweep_prepare(entries, nullptr, m, 4, ws->bases, ws->mvis, s);
+    radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s);
+    uint32_t *k0 = ws->ek2, *v0 = ws->ev2, *k1 = ws->ek, *v1 = ws->ev;
+    for (int shift = 8; shift < 32; shift += 8) {
+        radix_pass(OsSrc{k0, v0, nullptr, nullptr}, k1, v1, ws->mvis, m, shift,
+                   ws->bases + RADIX * (shift / 8), ws, d_status, s);
         uint32_t* t = k0; k0 = k1; k1 = t;
         t = v0; v0 = v1; v1 = t;
     }
@@ -755,41 +845,48 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     const float4* pco = reinterpret_cast<const float4*>(pre->conic);
     const unsigned eg = (unsigned)ceil_div(m, 256);
     if (!tight)
-        gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->tiles_s);
+        gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
     else if (vs->tile_w == 16)
-        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
+        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+                                               ws->tiles_s);
     else if (vs->tile_w == 8)
-        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
+        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+                                              ws->tiles_s);
     else
-        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, n, *vs, ws->tiles_s);
+        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+                                              ws->tiles_s);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
     scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums,
                                                             ws->offsets);
-    // 3. emission; the value buffers alternate so that the last pass lands in vals
+    // 3. emission; the value buffers alternate so that the last pass lands in vals.
+    //    Emission also counts the tile-id digits of the instances it writes.
     const int passes = tile_passes(vs->n_tiles);
     uint32_t *ka = ws->ak, *kb = ws->bk;
     uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
+    uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
+    cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * OS_MAX_DIGITS, s);
     if (tight) {
         if (vs->tile_w == 16)
             emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                        m, n, d_status, capacity, *vs, ka, va);
+                                                        m, n, d_status, capacity, *vs, ka, va, passes, tbases);
         else if (vs->tile_w == 8)
             emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                       m, n, d_status, capacity, *vs, ka, va);
+                                                       m, n, d_status, capacity, *vs, ka, va, passes, tbases);
         else
             emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                       m, n, d_status, capacity, *vs, ka, va);
+                                                       m, n, d_status, capacity, *vs, ka, va, passes, tbases);
     } else {
         emit_pairs<<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, m, n, d_status,
-                                      capacity, *vs, ka, va);
+                                      capacity, *vs, ka, va, passes, tbases);
     }
     // 4. tile-id passes over the K instances
-    if (passes > 0) onesweep_prepare(ka, d_status, capacity, passes, ws->bases + OS_MAX_DIGITS * RADIX, s);
+    const int64_t* kcount = d_status + LGS_ST_NUM_INSTANCES;
+    if (passes > 0) onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
     for (int p = 0; p < passes; ++p) {
-        radix_pass(ka, va, kb, vb, d_status, capacity, 8 * p, ws->bases + (OS_MAX_DIGITS + p) * RADIX, ws,
-                   d_status, s);
+        radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p,
+                   tbases + p * RADIX, ws, d_status, s);
         uint32_t* t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }
