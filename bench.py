@@ -259,15 +259,16 @@ def recorded_traffic(kernel="render_localgs_16x16"):
 
 def run_batched(dev, steps):
     """The batched workload: 3M clustered SH3 Gaussians, 64 cameras of uneven
-    resolution; forward + backward captured in one CUDA graph, tile shape and
-    persistent launch picked by the autotuner, graph replays timed."""
+    resolution; forward + backward captured in one CUDA graph with tight-box
+    emission, tile shape and persistent launch picked by the autotuner, graph
+    replays timed."""
     import torch
     from paper_2606_16566_gb300 import batch, lgs, scenes
     sc, cams = scenes.batched()
     g = lgs.to_device(sc, dev)
     del sc
-    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False)
-    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True)
+    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False, tight=True)
+    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True, tight=True)
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -284,7 +285,8 @@ def run_batched(dev, steps):
     st = r.check()
     ms = float(np.mean(ts))
     P = lgs.n_pixels(cams)
-    out = {"workload": "batched-3M-sh3-64-uneven-views-fwd+bwd-graph", "frames_s": len(cams) / (ms * 1e-3),
+    out = {"workload": "batched-3M-sh3-64-uneven-views-fwd+bwd-graph", "emission": "tight",
+           "frames_s": len(cams) / (ms * 1e-3),
            "mpix_s": P / 1e6 / (ms * 1e-3), "ms_per_step": ms, "instances_K": int(st[2]),
            "tile": list(tune["tile"]), "persistent": tune["persistent"], "autotune": tune["timings"],
            "replays": len(ts)}

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
     __shared__ float2 sDE[BWD_BATCH];
     __shared__ float4 sC[BWD_BATCH];
     __shared__ uint8_t sM[BWD_BATCH];
+    __shared__ uint8_t sL[8][BWD_BATCH];
     __shared__ uint32_t sId[BWD_BATCH];
     __shared__ float sG[BWD_BATCH][9];
     __shared__ uint32_t sLast[8];
@@ -160,14 +161,21 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
         }
         __syncthreads();
         if (wlast > (uint32_t)begin) {
-            for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+            // the warp's list of the batch (set mask bits up to its last
+            // contributor), compacted in order and walked back to front
+            uint8_t* sLw = sL[warp];
+            int nl = 0;
+            for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
-                uint32_t bits = __ballot_sync(0xffffffffu, jj < nb && ((sM[jj] >> warp) & 1u) &&
-                                                               (uint32_t)(begin + jj) < wlast);
-                while (bits) {
-                    const int k = 31 - __clz(bits);
-                    bits &= ~(1u << k);
-                    const int g = c0 + k;
+                const bool hit = jj < nb && ((sM[jj] >> warp) & 1u) && (uint32_t)(begin + jj) < wlast;
+                const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) sLw[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
+                nl += __popc(bal);
+            }
+            __syncwarp();
+            {
+                for (int i = nl - 1; i >= 0; --i) {
+                    const int g = sLw[i];
                     const float4 V = sV[g];
                     const float2 DE = sDE[g];
                     const float4 col = sC[g];

@@ -15,8 +15,9 @@
 //      tight box of the Gaussian's ellipse a x~^2 + 2b x~y~ + c y~^2 = tau,
 //      tau = 2 ln(255 o), restricted to the tile column (Cases A/B/C), and turns
 //      its vertical span into an 8-bit mask of warp strips. Each warp then
-//      compacts the batch with __ballot_sync on its mask bit and walks only
-//      the set bits, so culled Gaussians cost no issue slot at all.
+//      compacts the batch into its own index list (one __ballot_sync per 32
+//      candidates, written to shared memory) and walks that list with a plain
+//      counter, so culled Gaussians cost no issue slot in the blend loop.
 //  (3) warp-coherent blending (Sec. III-D): the per-pair data path is a fixed
 //      branch-free sequence (5 FMA dot product, ex2, clamp, predicated
 //      threshold/stop, w = alpha T, 3 FMA colour, 1 FMA transmittance); the
@@ -98,10 +99,11 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 
 // ------------------------------------------------------------------ Local-GS
 struct LocalSmem {
-    float4 sV[BATCH];   // (A, B, C, F), log2 domain
-    float2 sDE[BATCH];  // (D, E)
-    float4 sC[BATCH];   // (r, g, b, -)
-    uint8_t sM[BATCH];  // warp-strip mask
+    float4 sV[BATCH];       // (A, B, C, F), log2 domain
+    float2 sDE[BATCH];      // (D, E)
+    float4 sC[BATCH];       // (r, g, b, -)
+    uint8_t sM[BATCH];      // warp-strip mask
+    uint8_t sL[8][BATCH];   // per warp: batch indices of its set mask bits, in order
 };
 
 // Variants of the Local-GS tile loop:
@@ -162,20 +164,30 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
         __syncthreads();
         const int nb = (int)min((uint32_t)BATCH, t.count - b0);
         if (!warp_done) {
+            // compact the warp's list: the batch indices whose mask bit for this
+            // warp is set, in list order (one ballot per 32 candidates)
+            uint8_t* sL = S.sL[warp];
+            int nl = 0;
             for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
-                uint32_t bits = __ballot_sync(0xffffffffu, jj < nb && ((sM[jj] >> warp) & 1u));
-                while (bits) {
-                    const int k = __ffs(bits) - 1;
-                    bits &= bits - 1;
+                const bool hit = jj < nb && ((sM[jj] >> warp) & 1u);
+                const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) sL[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
+                nl += __popc(bal);
+            }
+            __syncwarp();
+            // walk it; the warp leaves once every lane is done (tested per 32)
+            for (int i0 = 0; i0 < nl && !warp_done; i0 += 32) {
+                const int iend = min(nl, i0 + 32);
+                for (int i = i0; i < iend; ++i) {
+                    const int g = sL[i];
                     if (VAR == VAR_LITERAL) {
-                        if (__all_sync(0xffffffffu, !t.inside || T < 1e-4f)) { bits = 0; done = true; break; }
+                        if (__all_sync(0xffffffffu, !t.inside || T < 1e-4f)) { done = true; break; }
                         if (COUNT) ++pairs;
                     } else if (COUNT) {
-                        if (__all_sync(0xffffffffu, done)) { bits = 0; break; }
+                        if (__all_sync(0xffffffffu, done)) break;
                         ++pairs;
                     }
-                    const int g = c0 + k;
                     const float4 V = sV[g];
                     const float2 DE = sDE[g];
                     const float4 col = sC[g];
@@ -196,14 +208,18 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                     const bool stop = valid && tT < 1e-4f;
                     const bool blend = valid && !stop;
                     done = done || stop;
-                    const float w = blend ? al * T : 0.f;
+                    // alpha of the pixel's blend (0 when it does not blend): the
+                    // colour and T updates need no further select, and
+                    // fma(-0, T, T) leaves T exactly as it was
+                    const float ab = blend ? al : 0.f;
+                    const float w = ab * T;
                     C0 = fmaf(col.x, w, C0);
                     C1 = fmaf(col.y, w, C1);
                     C2 = fmaf(col.z, w, C2);
-                    T = blend ? tT : T;
+                    T = fmaf(-ab, T, T);
                     last = blend ? (b0 + (uint32_t)g + 1u) : last;
                 }
-                if (__all_sync(0xffffffffu, done)) { warp_done = true; break; }
+                if (__all_sync(0xffffffffu, done)) warp_done = true;
             }
         }
         __syncthreads();
