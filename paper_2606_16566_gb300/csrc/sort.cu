@@ -37,7 +37,6 @@ constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 2048
 
 constexpr int RADIX = 256;
-constexpr int OS_MAX_DIGITS_E = 4;   // digit positions an emission histogram can hold
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -171,10 +170,7 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
                                                   const uint32_t* offsets, const uint64_t* rect,
                                                   int64_t m, int64_t n, const int64_t* status,
                                                   int64_t capacity, Views vs, uint32_t* tkey,
-                                                  uint32_t* tval, int npass, uint32_t* ghist) {
-    __shared__ uint32_t h[OS_MAX_DIGITS_E * RADIX];
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
-    __syncthreads();
+                                                  uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
     const int lane = threadIdx.x & 31;
@@ -222,16 +218,11 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
             const uint32_t oent = __shfl_sync(0xffffffffu, ent, own);
             if (e < total) {
                 const uint32_t ry = k / ow, rx = k - ry * ow;
-                const uint32_t tile = otoff + (oy0 + ry) * ogx + ox0 + rx;
-                tkey[start + e] = tile;
+                tkey[start + e] = otoff + (oy0 + ry) * ogx + ox0 + rx;
                 tval[start + e] = oent;
-                for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX + ((tile >> (8 * p)) & 0xffu)], 1u);
             }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
 // ------------------------------------------------------------------ tight-box emission
@@ -365,10 +356,7 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
                                                         const float4* xy, const float4* conic,
                                                         int64_t m, int64_t n, int64_t* status,
                                                         int64_t capacity, Views vs, uint32_t* tkey,
-                                                        uint32_t* tval, int npass, uint32_t* ghist) {
-    __shared__ uint32_t h[OS_MAX_DIGITS_E * RADIX];
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
-    __syncthreads();
+                                                        uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
     const int lane = threadIdx.x & 31;
@@ -404,11 +392,8 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
             for (uint32_t r = 0; r < k; ++r) {
                 const uint32_t q = pos + r;
                 if (q < total) {
-                    const uint32_t tile = otoff + ((uint32_t)rlo + r) * ogx + tx;
-                    tkey[start + q] = tile;
+                    tkey[start + q] = otoff + ((uint32_t)rlo + r) * ogx + tx;
                     tval[start + q] = oent;
-                    for (int p = 0; p < npass; ++p)
-                        atomicAdd(&h[p * RADIX + ((tile >> (8 * p)) & 0xffu)], 1u);
                 }
             }
             run += __shfl_sync(0xffffffffu, ik, 31);
@@ -417,14 +402,10 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
             for (uint32_t q = run + lane; q < total; q += 32) {
                 tkey[start + q] = 0u;
                 tval[start + q] = 0u;
-                for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX], 1u);
             }
             if (lane == 0) report_error(status, LGS_ERR_INTERNAL, (int64_t)total - (int64_t)run);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
 // ------------------------------------------------------------------ radix passes (onesweep)
@@ -455,7 +436,6 @@ constexpr uint64_t OS_PRE = 2ull << 62;
 constexpr uint64_t OS_VAL = (1ull << 62) - 1;
 constexpr int OS_SPIN_LIMIT = 1 << 20;
 constexpr int OS_MAX_DIGITS = 4;
-static_assert(OS_MAX_DIGITS == OS_MAX_DIGITS_E, "emission histograms cover every tile-id digit");
 
 // Where a pass reads its pairs: key/value arrays, or (k == nullptr) the
 // entries' tiles-touched and depth.
@@ -483,29 +463,94 @@ __device__ __forceinline__ bool os_load(const OsSrc& src, int64_t i, uint32_t& k
 
 // Per-digit-position histograms of the (kept) keys: ghist[p*256 + d] += count
 // of kept elements whose digit p (bits 8p..8p+7) is d, for p < npass; with a
-// synthesized source also the number of kept elements into *kept.
+// synthesized source also the number of kept elements into *kept. One private
+// histogram per warp; when all kept keys of a warp share a digit (the high
+// depth bytes often do), one atomic adds them all.
 __global__ void __launch_bounds__(256) onesweep_histogram(OsSrc src, const int64_t* cnt, int64_t count,
                                                           int npass, uint32_t* ghist, int64_t* kept) {
-    __shared__ uint32_t h[OS_MAX_DIGITS * RADIX];
+    __shared__ uint32_t h[8][OS_MAX_DIGITS][RADIX];
     __shared__ uint32_t s_kept;
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) h[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * OS_MAX_DIGITS * RADIX; i += blockDim.x) (&h[0][0][0])[i] = 0;
     if (threadIdx.x == 0) s_kept = 0;
     __syncthreads();
     const int64_t K = pass_count(cnt, count);
     uint32_t my_kept = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k, v;
-        if (!os_load(src, i, k, v)) continue;
-        ++my_kept;
-        for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX + ((k >> (8 * p)) & 0xffu)], 1u);
+    for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < K; base += (int64_t)gridDim.x * 256) {
+        const int64_t i = base + lane;
+        uint32_t k = 0, v;
+        const bool ok = i < K && os_load(src, i, k, v);
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (bal == 0u) continue;
+        my_kept += ok;
+        const int leader = __ffs(bal) - 1;
+        for (int p = 0; p < npass; ++p) {
+            const uint32_t d = (k >> (8 * p)) & 0xffu;
+            const uint32_t first = __shfl_sync(0xffffffffu, d, leader);
+            if (__all_sync(0xffffffffu, !ok || d == first)) {
+                if (lane == leader) atomicAdd(&h[warp][p][first], (uint32_t)__popc(bal));
+            } else if (ok) {
+                atomicAdd(&h[warp][p][d], 1u);
+            }
+        }
     }
     if (kept && my_kept) atomicAdd(&s_kept, my_kept);
     __syncthreads();
-    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += (&h[w][0][0])[i];
+        if (sum) atomicAdd(&ghist[i], sum);
+    }
     if (kept && threadIdx.x == 0 && s_kept)
         atomicAdd(reinterpret_cast<unsigned long long*>(kept), (unsigned long long)s_kept);
+}
+
+// Digit histograms of a key array (the tile ids of the instances): 16-B loads,
+// one private histogram per warp, and a warp-uniform fast path -- when all 128
+// digits a warp loads at once are equal (instances of neighbouring Gaussians
+// mostly share the high tile-id byte) one atomic adds them all.
+__global__ void __launch_bounds__(256) key_histogram(const uint32_t* keys, const int64_t* cnt,
+                                                     int64_t count, int npass, uint32_t* ghist) {
+    __shared__ uint32_t h[8][OS_MAX_DIGITS][RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * OS_MAX_DIGITS * RADIX; i += blockDim.x) (&h[0][0][0])[i] = 0;
+    __syncthreads();
+    const int64_t K = pass_count(cnt, count);
+    const int64_t n4 = K / 4;
+    const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+    for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < n4; base += (int64_t)gridDim.x * 256) {
+        const int64_t q = base + lane;
+        const bool ok = q < n4;
+        const uint4 v = ok ? k4[q] : make_uint4(0u, 0u, 0u, 0u);
+        const int nok = __popc(__ballot_sync(0xffffffffu, ok));
+        for (int p = 0; p < npass; ++p) {
+            const int sh = 8 * p;
+            const uint32_t d0 = (v.x >> sh) & 0xffu, d1 = (v.y >> sh) & 0xffu;
+            const uint32_t d2 = (v.z >> sh) & 0xffu, d3 = (v.w >> sh) & 0xffu;
+            const uint32_t first = __shfl_sync(0xffffffffu, d0, 0);
+            const bool uni = !ok || (d0 == first && d1 == first && d2 == first && d3 == first);
+            if (__all_sync(0xffffffffu, uni)) {
+                if (lane == 0) atomicAdd(&h[warp][p][first], 4u * (uint32_t)nok);
+            } else if (ok) {
+                atomicAdd(&h[warp][p][d0], 1u);
+                atomicAdd(&h[warp][p][d1], 1u);
+                atomicAdd(&h[warp][p][d2], 1u);
+                atomicAdd(&h[warp][p][d3], 1u);
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (int)(K - 4 * n4)) {       // the K mod 4 tail
+        const uint32_t k = keys[4 * n4 + threadIdx.x];
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[0][p][(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * RADIX; i += blockDim.x) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += (&h[w][0][0])[i];
+        if (sum) atomicAdd(&ghist[i], sum);
+    }
 }
 
 // In place: each digit position's 256 counts -> exclusive prefix (one block per position).
@@ -860,30 +905,32 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
     scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums,
                                                             ws->offsets);
-    // 3. emission; the value buffers alternate so that the last pass lands in vals.
-    //    Emission also counts the tile-id digits of the instances it writes.
+    // 3. emission; the value buffers alternate so that the last pass lands in vals
     const int passes = tile_passes(vs->n_tiles);
     uint32_t *ka = ws->ak, *kb = ws->bk;
     uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
-    uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
-    cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * OS_MAX_DIGITS, s);
     if (tight) {
         if (vs->tile_w == 16)
             emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                        m, n, d_status, capacity, *vs, ka, va, passes, tbases);
+                                                        m, n, d_status, capacity, *vs, ka, va);
         else if (vs->tile_w == 8)
             emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                       m, n, d_status, capacity, *vs, ka, va, passes, tbases);
+                                                       m, n, d_status, capacity, *vs, ka, va);
         else
             emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
-                                                       m, n, d_status, capacity, *vs, ka, va, passes, tbases);
+                                                       m, n, d_status, capacity, *vs, ka, va);
     } else {
         emit_pairs<<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, m, n, d_status,
-                                      capacity, *vs, ka, va, passes, tbases);
+                                      capacity, *vs, ka, va);
     }
     // 4. tile-id passes over the K instances
     const int64_t* kcount = d_status + LGS_ST_NUM_INSTANCES;
-    if (passes > 0) onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
+    uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
+    if (passes > 0) {
+        cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * passes, s);
+        key_histogram<<<152 * 4, 256, 0, s>>>(ka, kcount, capacity, passes, tbases);
+        onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
+    }
     for (int p = 0; p < passes; ++p) {
         radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p,
                    tbases + p * RADIX, ws, d_status, s);
