@@ -99,12 +99,23 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 
 // ------------------------------------------------------------------ Local-GS
 struct LocalSmem {
-    float4 sV[BATCH];       // (A, B, C, F), log2 domain
-    float2 sDE[BATCH];      // (D, E)
-    float4 sC[BATCH];       // (r, g, b, -)
-    uint8_t sM[BATCH];      // warp-strip mask
-    uint8_t sL[8][BATCH];   // per warp: batch indices of its set mask bits, in order
+    float4 raw[2][3][BATCH];  // double-buffered cp.async landing zone: xy, conic, rgb records
+    float4 sV[BATCH];         // (A, B, C, F), log2 domain
+    float2 sDE[BATCH];        // (D, E)
+    float4 sC[BATCH];         // (r, g, b, -)
+    uint8_t sM[BATCH];        // warp-strip mask
+    uint8_t sL[8][BATCH];     // per warp: batch indices of its set mask bits, in order
 };
+
+// 16-byte asynchronous global -> shared copy (cp.async, cached in L2 only:
+// neighbouring tiles read the same Gaussians from L2) and its group fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Variants of the Local-GS tile loop:
 //  VAR_CONTRACT: the per-pixel definition (1/255 skip and stop as predicates),
@@ -141,14 +152,33 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     bool warp_done = __all_sync(0xffffffffu, done);
     uint32_t pairs = 0;
 
-    for (uint32_t b0 = 0; b0 < t.count; b0 += BATCH) {
+    // Staging: thread i copies the three 16-B records of list entry b0 + i with
+    // cp.async into buffer (b0 / BATCH) & 1, one batch ahead, so the gathers of
+    // batch b+1 are in flight while batch b blends. A thread reads back only
+    // the slots it copied itself, so its own group fence orders them.
+    const int ti = threadIdx.x;
+    auto stage = [&](uint32_t b, int buf) {
+        const uint32_t jj = b + (uint32_t)ti;
+        if (jj < t.count) {
+            const uint32_t id = p.vals[t.start + jj];
+            cp_async16(&S.raw[buf][0][ti], p.xy + id);
+            cp_async16(&S.raw[buf][1][ti], p.conic + id);
+            cp_async16(&S.raw[buf][2][ti], p.rgb + id);
+        }
+        cp_async_commit();
+    };
+    if (t.count > 0 && !__syncthreads_and(warp_done)) stage(0, 0);
+    int buf = 0;
+    for (uint32_t b0 = 0; b0 < t.count; b0 += BATCH, buf ^= 1) {
         if (__syncthreads_and(warp_done)) break;
+        if (b0 + BATCH < t.count) stage(b0 + BATCH, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
         const uint32_t j = b0 + threadIdx.x;
         if (j < t.count) {
-            const uint32_t id = p.vals[t.start + j];
-            const float4 xy = p.xy[id];
-            const float4 co = p.conic[id];
-            const float4 col = p.rgb[id];
+            const float4 xy = S.raw[buf][0][ti];
+            const float4 co = S.raw[buf][1][ti];
+            const float4 col = S.raw[buf][2][ti];
             const float dx = __fadd_rn(xy.x - Ox, xy.z);
             const float dy = __fadd_rn(xy.y - Oy, xy.w);
             const float Dn = fmaf(co.x, dx, co.y * dy);
@@ -224,6 +254,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
     write_pixel(vs, p, t, C0, C1, C2, T, last);
     if (COUNT && lane == 0 && pairs)
         atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_PAIRS),
