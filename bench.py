@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--views", type=int, default=8, help="views of the outdoor workload (profiling)")
     p.add_argument("--mode", default="localgs", choices=["localgs", "plain", "literal", "global"])
     p.add_argument("--no-batched", action="store_true", help="skip the 64-view batched workload")
+    p.add_argument("--no-indoor", action="store_true", help="skip the indoor training step")
+    p.add_argument("--no-scale", action="store_true", help="skip the 30M-Gaussian scale scene")
     p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
     p.add_argument("--tight", action="store_true", help="with --profile: tight-box emission")
     return p.parse_args()
@@ -295,6 +297,123 @@ def run_batched(dev, steps):
     return out, len(ts)
 
 
+def _graph_ms(graph, flush, reps):
+    import torch
+    ts = []
+    for i in range(reps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts)), len(ts)
+
+
+def run_indoor(dev, steps):
+    """The indoor training step: 2.8M SH3 Gaussians on room walls, one 1332x876
+    view; forward, L1 loss against a seeded random target, full adjoint, all in
+    one CUDA graph (tight-box emission)."""
+    import torch
+    from paper_2606_16566_gb300 import batch, lgs, scenes
+    sc, cams = scenes.indoor()
+    g = lgs.to_device(sc, dev)
+    del sc
+    r = batch.Renderer(g, cams, backward=True, tight=True)
+    target = torch.rand(r.rgb.shape, generator=torch.Generator(device=dev).manual_seed(7), device=dev)
+    diff = torch.empty_like(r.rgb)
+    inv_n = 1.0 / r.rgb.numel()
+
+    def step():
+        r.forward()
+        torch.sub(r.rgb, target, out=diff)
+        torch.sign(diff, out=r.d_rgb)
+        r.d_rgb.mul_(inv_n)
+        r.backward()
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms, n = _graph_ms(graph, flush, max(3, steps // 4))
+    st = r.check()
+    loss = float(diff.abs().mean().item())
+    P = lgs.n_pixels(cams)
+    out = {"workload": "indoor-2.8M-sh3-1332x876-training-step (fwd + L1 + bwd, graph, tight)",
+           "steps_s": 1e3 / ms, "ms_per_step": ms, "mpix_s": P / 1e6 / (ms * 1e-3), "instances_K": int(st[2]),
+           "l1_loss": loss, "replays": n}
+    del r, g, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_scale(dev, steps):
+    """The scale scene: 30M SH3 Gaussians (256 clusters + background), 16 views
+    of 1920x1080 in one batch; forward with per-stage events, forward+backward
+    as one graph replay, the warp-culled fraction of the Local-GS schedule, and
+    the HBM rate of preprocess (algorithmic bytes: 236 B read per Gaussian,
+    69 B written per (view, Gaussian) entry)."""
+    import torch
+    from paper_2606_16566_gb300 import batch, lgs, scenes
+    from paper_2606_16566_gb300 import _lib as L
+    sc, cams = scenes.scale()
+    g = lgs.to_device(sc, dev)
+    del sc
+    n, V = g["means"].shape[0], len(cams)
+    r = batch.Renderer(g, cams, backward=True, tight=True)
+    cfg_count = lgs.config(r.tile, "localgs", L.FLAG_TIGHT | L.FLAG_COUNT)
+    r.forward()
+    lgs.render_fwd(r.pre, r.vals, r.ranges, cams, cfg_count, r.rgb, r.T, r.nc, r.status)
+    st = r.check()
+    pairs, cands = int(st[L.ST_PAIRS]), int(st[L.ST_CANDIDATES])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stage = []
+    for i in range(max(3, steps // 8) + 1):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        r.status.zero_()
+        lgs.preprocess(r.g, r.carr, r.cfg, out=r.pre, status=r.status)
+        e[1].record()
+        lgs.sort(r.pre, r.n, r.cams, r.cfg, r.capacity, None, r.vals, r.ranges, r.ws, r.status, with_keys=False)
+        e[2].record()
+        lgs.render_fwd(r.pre, r.vals, r.ranges, r.cams, r.cfg, r.rgb, r.T, r.nc, r.status)
+        e[3].record()
+        torch.cuda.synchronize()
+        if i >= 1:
+            stage.append([e[k].elapsed_time(e[k + 1]) for k in range(3)])
+    st = r.check()
+    K = int(st[L.ST_NUM_INSTANCES])
+    sm = np.mean(np.array(stage), 0)
+    ms_f = float(sm.sum())
+    r.d_rgb.fill_(1.0 / r.d_rgb.numel())
+    r.capture()
+    ms_fb, nrep = _graph_ms(r.graph, flush, max(3, steps // 8))
+    r.check()
+    P = lgs.n_pixels(cams)
+    pre_bytes = n * 236 + n * V * 69
+    out = {"workload": "scale-30M-sh3-16x1920x1080 (tight)", "frames_s": V / (ms_f * 1e-3),
+           "mpix_s": P / 1e6 / (ms_f * 1e-3), "ms_per_step": ms_f,
+           "stage_ms": {"preprocess": float(sm[0]), "sort": float(sm[1]), "render": float(sm[2])},
+           "fwd_bwd": {"frames_s": V / (ms_fb * 1e-3), "ms_per_step": ms_fb, "replays": nrep},
+           "instances_K": K, "culled_warp_fraction": 1.0 - pairs / 32.0 / max(cands, 1),
+           "warp_candidates": cands, "pairs": pairs,
+           "preprocess_hbm_gbs": pre_bytes / (sm[0] * 1e-3) / 1e9,
+           "preprocess_bytes": pre_bytes}
+    del r, g
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -466,6 +585,8 @@ def run_ours(args, rank, world):
     batched, n_batched = (None, 0)
     if not args.no_batched:
         batched, n_batched = run_batched(dev, args.steps)
+    indoor = None if args.no_indoor else run_indoor(dev, args.steps)
+    scale = None if args.no_scale else run_scale(dev, args.steps)
     if rank != 0:
         return
     emission = "tight" if head.endswith("tight") else "rect"
@@ -494,6 +615,8 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched": batched,
+        "indoor": indoor,
+        "scale": scale,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)

@@ -74,7 +74,9 @@ typedef int32_t lgs_status;
 #define LGS_ST_PAIRS 4          /* pixel-Gaussian pairs of the render schedule (LGS_FLAG_COUNT) */
 #define LGS_ST_QUEUE 5          /* work-queue counter of the persistent render (library-owned) */
 #define LGS_ST_QUEUE_BWD 6      /* work-queue counter of the persistent backward (library-owned) */
-#define LGS_ST_SPARE 7
+#define LGS_ST_CANDIDATES 7     /* (warp, Gaussian) candidates the Local-GS render's warps scanned
+                                   before their exit (LGS_FLAG_COUNT); 1 - PAIRS/32/CANDIDATES is
+                                   the fraction the warp mask culled */
 
 /* Pinhole camera. Pixel (x, y) is sampled at the integer position (x, y);
  * u = fx * X/Z + cx, v = fy * Y/Z + cy for a camera-space point (X, Y, Z).
@@ -264,6 +266,19 @@ lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams, int32_
                           const uint32_t* ranges, const float* final_T, const uint32_t* n_contrib,
                           const float* dL_drgb, const float* dL_dfinal_T, const lgs_grads* grads,
                           int64_t* d_status, void* stream);
+
+/* Failure-detection self-test (no counterpart in the paper). Every device-side
+ * wait of the library (the look-back of the sort's radix passes) is bounded:
+ * after a spin limit it records LGS_ERR_TIMEOUT in d_status and returns
+ * instead of hanging. This entry point makes one such wait run out on purpose:
+ * it launches a single radix-pass block that waits on a predecessor that never
+ * runs, with the given spin limit (polls of an L2 word, ~0.5 us each), inside
+ * the caller's workspace of LGS_SELFTEST_WORKSPACE_BYTES (device, 256-B
+ * aligned). Afterwards d_status holds LGS_ERR_TIMEOUT with detail 1. Nothing
+ * faults or traps; the context stays usable. */
+#define LGS_SELFTEST_WORKSPACE_BYTES (160ull << 10)
+lgs_status lgs_selftest_wait_timeout(int32_t spin_limit, void* workspace, size_t workspace_bytes,
+                                     int64_t* d_status, void* stream);
 
 /* Copies the LGS_STATUS_WORDS device status words into h_status after
  * synchronising `stream`. Returns LGS_ERR_CUDA if the copy fails. */

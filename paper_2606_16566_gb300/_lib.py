@@ -24,8 +24,9 @@ LGS_ERR_INTERNAL = 8
 LGS_MAX_VIEWS = 64
 SORT_STATIC_MAX_ENTRIES = 1 << 18
 SORT_STATIC_MAX_INSTANCES = 1 << 20
+SELFTEST_WORKSPACE_BYTES = 160 << 10
 LGS_STATUS_WORDS = 8
-ST_CODE, ST_DETAIL, ST_NUM_INSTANCES, ST_NONFINITE, ST_PAIRS, ST_QUEUE, ST_QUEUE_BWD, ST_SPARE = range(8)
+ST_CODE, ST_DETAIL, ST_NUM_INSTANCES, ST_NONFINITE, ST_PAIRS, ST_QUEUE, ST_QUEUE_BWD, ST_CANDIDATES = range(8)
 
 MODE_LOCALGS = 0
 MODE_PLAIN = 1
@@ -87,6 +88,7 @@ SIGNATURES = {
                                         ctypes.c_int32, ctypes.POINTER(lgs_config),
                                         ctypes.POINTER(lgs_pre_out), _vp, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.POINTER(lgs_grads), _vp, _vp]),
+    "lgs_selftest_wait_timeout": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.c_size_t, _vp, _vp]),
     "lgs_read_status": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64), _vp]),
     "lgs_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "lgs_version": (ctypes.c_int32, []),

@@ -150,7 +150,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     uint32_t last = 0;
     bool done = !t.inside;
     bool warp_done = __all_sync(0xffffffffu, done);
-    uint32_t pairs = 0;
+    uint32_t pairs = 0, cands = 0;
 
     // Staging: thread i copies the three 16-B records of list entry b0 + i with
     // cp.async into buffer (b0 / BATCH) & 1, one batch ahead, so the gathers of
@@ -193,6 +193,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)BATCH, t.count - b0);
+        if (COUNT && !warp_done) cands += (uint32_t)nb;
         if (!warp_done) {
             // compact the warp's list: the batch indices whose mask bit for this
             // warp is set, in list order (one ballot per 32 candidates)
@@ -259,6 +260,9 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     if (COUNT && lane == 0 && pairs)
         atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_PAIRS),
                   (unsigned long long)pairs * 32ull);
+    if (COUNT && lane == 0 && cands)
+        atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_CANDIDATES),
+                  (unsigned long long)cands);
 }
 
 // One CTA per tile.

@@ -418,8 +418,8 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
 // (AGG) or its inclusive prefix (PRE); the walk stops at the first PRE. Only
 // then does it rank its keys stably and scatter them. A block only waits on
 // tiles that were handed out before its own and therefore are already
-// running; every wait is bounded: after OS_SPIN_LIMIT polls the block records
-// LGS_ERR_TIMEOUT and continues. The digit bases of all passes come from one
+// running; every wait is bounded: after spin_limit polls (OS_SPIN_LIMIT, about
+// a second of L2 round trips) the block records LGS_ERR_TIMEOUT and continues. The digit bases of all passes come from one
 // histogram kernel over the input keys (digits of later passes are counted on
 // the same keys, since a pass only permutes them).
 //
@@ -580,7 +580,7 @@ struct OneSmem {
 __global__ void __launch_bounds__(OS_THREADS, 3) onesweep_pass(
     OsSrc src, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* cnt,
     int64_t count, int shift, const uint32_t* bases, unsigned long long* look, uint32_t* tile_counter,
-    int64_t* err_status) {
+    int64_t* err_status, int spin_limit) {
     constexpr int NW = OS_THREADS / 32;
     constexpr int PER_WARP = OS_TILE / NW;      // 512
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(OS_THREADS, 3) onesweep_pass(
             const uint64_t w = *reinterpret_cast<volatile unsigned long long*>(look + j * RADIX + t);
             const uint64_t f = w & ~OS_VAL;
             if (f == 0) {
-                if (++spins > OS_SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     report_error(err_status, LGS_ERR_TIMEOUT, (int64_t)tile);
                     break;
                 }
@@ -838,7 +838,7 @@ static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const i
     cudaMemsetAsync(ws->look, 0, sizeof(unsigned long long) * RADIX * (size_t)nt, s);
     cudaMemsetAsync(ws->counters, 0, sizeof(uint32_t), s);
     onesweep_pass<<<(unsigned)nt, OS_THREADS, sizeof(OneSmem), s>>>(
-        src, kout, vout, cnt, count, shift, bases, ws->look, ws->counters, d_status);
+        src, kout, vout, cnt, count, shift, bases, ws->look, ws->counters, d_status, OS_SPIN_LIMIT);
 }
 
 }  // namespace lgs
@@ -1029,4 +1029,35 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
     sort_ws_layout(m, capacity, static_cast<char*>(scratch), &ws);
     return sort_enqueue(pre, n, &vs, capacity, keys, vals, ranges, &ws, d_status,
                         static_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------------ failure-detection self-test
+// Runs one onesweep block that is handed tile index 1 of a two-tile pass whose
+// tile 0 never runs: its look-back waits on a word that nothing writes, gives
+// up after spin_limit polls, records LGS_ERR_TIMEOUT (detail = 1) and finishes
+// its pass (its output is meaningless but stays inside the scratch buffer).
+extern "C" lgs_status lgs_selftest_wait_timeout(int32_t spin_limit, void* workspace,
+                                               size_t workspace_bytes, int64_t* d_status,
+                                               void* stream) {
+    if (!workspace || !d_status || spin_limit < 0) return LGS_ERR_ARG;
+    if (workspace_bytes < (size_t)LGS_SELFTEST_WORKSPACE_BYTES) return LGS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return LGS_ERR_ALIGN;
+    char* w = static_cast<char*>(workspace);
+    uint32_t* kin = reinterpret_cast<uint32_t*>(w);
+    uint32_t* vin = kin + 2 * OS_TILE;
+    uint32_t* kout = vin + 2 * OS_TILE;
+    uint32_t* vout = kout + 2 * OS_TILE;
+    unsigned long long* look = reinterpret_cast<unsigned long long*>(vout + 2 * OS_TILE);
+    uint32_t* bases = reinterpret_cast<uint32_t*>(look + 2 * RADIX);
+    uint32_t* counter = bases + RADIX;
+    static_assert(8 * 2 * OS_TILE * 4 / 2 + 2 * RADIX * 8 + RADIX * 4 + 4 <= LGS_SELFTEST_WORKSPACE_BYTES,
+                  "self-test workspace");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(workspace, 0, LGS_SELFTEST_WORKSPACE_BYTES, s) != cudaSuccess) return LGS_ERR_CUDA;
+    if (cudaMemsetAsync(counter, 1, 1, s) != cudaSuccess) return LGS_ERR_CUDA;   // first tile handed out: 1
+    cudaFuncSetAttribute(onesweep_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(OneSmem));
+    onesweep_pass<<<1, OS_THREADS, sizeof(OneSmem), s>>>(OsSrc{kin, vin, nullptr, nullptr}, kout, vout,
+                                                          nullptr, 2 * OS_TILE, 0, bases, look, counter,
+                                                          d_status, spin_limit);
+    return cuda_status(cudaGetLastError());
 }

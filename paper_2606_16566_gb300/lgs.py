@@ -241,6 +241,17 @@ class RenderFunction(torch.autograd.Function):
         return gr["means"], gr["scales"], gr["quats"], gr["opacities"], gr["sh"], None, None, None
 
 
+def selftest_wait_timeout(spin_limit=1000, status=None, stream=None) -> np.ndarray:
+    """Makes one bounded device wait run out (lgs_selftest_wait_timeout) and
+    returns the status words it leaves."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty(L.SELFTEST_WORKSPACE_BYTES, dtype=torch.uint8, device=dev)
+    status = status if status is not None else new_status(dev)
+    L.check(L.load().lgs_selftest_wait_timeout(int(spin_limit), _ptr(ws), ws.numel(), _ptr(status),
+                                               _stream(stream)), "lgs_selftest_wait_timeout")
+    return read_status(status, stream)
+
+
 def read_status(status, stream=None) -> np.ndarray:
     h = (ctypes.c_int64 * L.LGS_STATUS_WORDS)()
     L.check(L.load().lgs_read_status(_ptr(status), h, _stream(stream)), "lgs_read_status")

@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 def test_status_strings_and_version():
     lib = L.load()
     assert lib.lgs_version() >= 1
-    for code in range(8):
+    for code in range(9):
         assert lib.lgs_status_string(code)
     assert b"capacity" in lib.lgs_status_string(L.LGS_ERR_CAPACITY)
 
@@ -64,3 +64,13 @@ def test_host_side_argument_checks_need_no_gpu():
                         fake, 1, fake, None) == L.LGS_ERR_ARG
     assert lib.lgs_sort_workspace_size(10, 100) > 0
     assert pre.xy is None
+
+
+def test_selftest_argument_checks_need_no_gpu():
+    lib = L.load()
+    assert lib.lgs_selftest_wait_timeout(10, None, 0, None, None) == L.LGS_ERR_ARG
+    fake = ctypes.c_void_p(256)
+    assert lib.lgs_selftest_wait_timeout(10, fake, 1024, fake, None) == L.LGS_ERR_ARG
+    assert lib.lgs_selftest_wait_timeout(-1, fake, L.SELFTEST_WORKSPACE_BYTES, fake, None) == L.LGS_ERR_ARG
+    assert lib.lgs_selftest_wait_timeout(10, ctypes.c_void_p(260), L.SELFTEST_WORKSPACE_BYTES, fake,
+                                         None) == L.LGS_ERR_ALIGN
