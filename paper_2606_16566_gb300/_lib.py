@@ -120,6 +120,18 @@ def load(build_if_missing: bool = True):
     return L
 
 
+def load_checked():
+    """The bounds-checked test build (LGS_CHECKED), built on first use, with the
+    same signatures; it does not replace the library load() returns."""
+    path = _build.build(checked=True)
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
 class LgsError(RuntimeError):
     def __init__(self, code, what=""):
         msg = load().lgs_status_string(code).decode()

@@ -46,6 +46,7 @@ struct BwdParams {
     float* g_xy;      // [M,2]
     float* g_conic;   // [M,4]
     float* g_rgb;     // [M,3]
+    int64_t* status;
 };
 
 __device__ __forceinline__ float ex2_approx_b(float x) {
@@ -110,7 +111,9 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
     const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
     const float xl = (float)lx - 0.5f * (TW - 1), yl = (float)ly - 0.5f * (TH - 1);
     const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
-    const uint2 r = p.ranges[tile];
+    uint2 r = p.ranges[tile];
+    if (!LGS_CHECK(r.x <= r.y && (r.y == r.x || (int64_t)r.y <= p.status[LGS_ST_NUM_INSTANCES]), 21, p.status))
+        r.y = r.x;
 
     float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, tail = 0.f;
     uint32_t last = 0;
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs)
     uint32_t tlast = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) tlast = max(tlast, sLast[w]);
+    if (!LGS_CHECK(tlast <= r.y - r.x, 22, p.status)) tlast = r.y - r.x;
 
     for (int end = (int)tlast; end > 0; end -= BWD_BATCH) {
         const int begin = max(0, end - BWD_BATCH);
@@ -280,7 +284,9 @@ __global__ void __launch_bounds__(256) render_bwd_plain(BwdParams p, Views vs) {
     const int px = X0 + lane % TW, py = Y0 + warp * (TH / 8) + lane / TW;
     const bool inside = px < c.W && py < c.H;
     const float pxf = (float)px, pyf = (float)py;
-    const uint2 r = p.ranges[tile];
+    uint2 r = p.ranges[tile];
+    if (!LGS_CHECK(r.x <= r.y && (r.y == r.x || (int64_t)r.y <= p.status[LGS_ST_NUM_INSTANCES]), 21, p.status))
+        r.y = r.x;
 
     float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, tail = 0.f;
     uint32_t last = 0;
@@ -303,6 +309,7 @@ __global__ void __launch_bounds__(256) render_bwd_plain(BwdParams p, Views vs) {
     uint32_t tlast = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) tlast = max(tlast, sLast[w]);
+    if (!LGS_CHECK(tlast <= r.y - r.x, 22, p.status)) tlast = r.y - r.x;
 
     for (int end = (int)tlast; end > 0; end -= BWD_BATCH) {
         const int begin = max(0, end - BWD_BATCH);
@@ -665,6 +672,7 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     bp.g_xy = grads->xy2d;
     bp.g_conic = grads->conic2d;
     bp.g_rgb = grads->rgb2d;
+    bp.status = d_status;
     if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
     if (cfg->tile_w == 16) launch_render_bwd<16, 16>(bp, vs, cfg->mode, s);
     else if (cfg->tile_w == 8) launch_render_bwd<8, 32>(bp, vs, cfg->mode, s);

@@ -46,6 +46,17 @@ __device__ __forceinline__ void report_error(int64_t* st, int64_t code, int64_t 
         atomicExch(w + LGS_ST_DETAIL, (unsigned long long)detail);
 }
 
+// Bounds checks of the LGS_CHECKED build (a test build; compiled out otherwise):
+// a failed check records LGS_ERR_INTERNAL with detail 1000 + site in the status
+// words and the caller skips the access, so an index bug shows up as a status
+// code instead of a memory fault.
+#ifdef LGS_CHECKED
+#define LGS_CHECK(cond, site, st) \
+    ((cond) ? true : (::lgs::report_error((st), LGS_ERR_INTERNAL, 1000 + (site)), false))
+#else
+#define LGS_CHECK(cond, site, st) true
+#endif
+
 // ---------------------------------------------------------------- float pairs
 // Unevaluated sums hi + lo of two floats (Dekker / Knuth error-free
 // transformations). The __f*_rn intrinsics keep the compiler from contracting

@@ -137,7 +137,12 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     float2* sDE = S.sDE;
     float4* sC = S.sC;
     uint8_t* sM = S.sM;
-    const TileCtx t = tile_ctx<TW, TH>(vs, p, tile);
+    TileCtx t = tile_ctx<TW, TH>(vs, p, tile);
+    // the tile's list must lie inside the sorted instances (checked build; it
+    // assumes the status words of the lgs_sort call that made the lists)
+    if (!LGS_CHECK(t.start <= t.start + t.count &&
+                   (t.count == 0 || (int64_t)t.start + t.count <= p.status[LGS_ST_NUM_INSTANCES]), 20, p.status))
+        t.count = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool global_frame = VAR == VAR_GLOBAL;
     const float Ox = global_frame ? 0.f : (float)t.X0 + 0.5f * (TW - 1);

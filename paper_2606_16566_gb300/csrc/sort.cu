@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* t
 // (shuffles), and the stores of a warp land on consecutive addresses.
 __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const uint32_t* tiles,
                                                   const uint32_t* offsets, const uint64_t* rect,
-                                                  int64_t m, int64_t n, const int64_t* status,
+                                                  int64_t m, int64_t n, int64_t* status,
                                                   int64_t capacity, Views vs, uint32_t* tkey,
                                                   uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,8 +218,12 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
             const uint32_t oent = __shfl_sync(0xffffffffu, ent, own);
             if (e < total) {
                 const uint32_t ry = k / ow, rx = k - ry * ow;
-                tkey[start + e] = otoff + (oy0 + ry) * ogx + ox0 + rx;
-                tval[start + e] = oent;
+                const uint32_t tile = otoff + (oy0 + ry) * ogx + ox0 + rx;
+                if (LGS_CHECK((int64_t)start + e < capacity, 1, status) &&
+                    LGS_CHECK(tile < vs.n_tiles, 2, status) && LGS_CHECK(oent < (uint64_t)m, 3, status)) {
+                    tkey[start + e] = tile;
+                    tval[start + e] = oent;
+                }
             }
         }
     }
@@ -391,8 +395,10 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
             const uint32_t pos = run + ik - k;
             for (uint32_t r = 0; r < k; ++r) {
                 const uint32_t q = pos + r;
-                if (q < total) {
-                    tkey[start + q] = otoff + ((uint32_t)rlo + r) * ogx + tx;
+                const uint32_t tile = otoff + ((uint32_t)rlo + r) * ogx + tx;
+                if (q < total && LGS_CHECK((int64_t)start + q < capacity, 4, status) &&
+                    LGS_CHECK(tile < vs.n_tiles, 5, status) && LGS_CHECK(oent < (uint64_t)m, 6, status)) {
+                    tkey[start + q] = tile;
                     tval[start + q] = oent;
                 }
             }
@@ -682,16 +688,18 @@ __global__ void __launch_bounds__(OS_THREADS, 3) onesweep_pass(
         const uint32_t key = S.keys[j];
         const uint32_t d = (key >> shift) & 0xffu;
         const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
-        kout[gpos] = key;
-        vout[gpos] = S.vals[j];
+        if (LGS_CHECK((int64_t)gpos < K, 7, err_status)) {
+            kout[gpos] = key;
+            vout[gpos] = S.vals[j];
+        }
     }
 }
 
 // ------------------------------------------------------------------ ranges
 // Per-tile [start, end) of the sorted tile ids; each thread takes 4
 // consecutive instances (one 16-B load when all 4 lie below K).
-__global__ void __launch_bounds__(256) tile_ranges(const uint32_t* tkey, const int64_t* status,
-                                                   int64_t capacity, uint2* ranges) {
+__global__ void __launch_bounds__(256) tile_ranges(const uint32_t* tkey, int64_t* status,
+                                                   int64_t capacity, uint32_t n_tiles, uint2* ranges) {
     const int64_t K = sort_count(status, capacity);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * q < K;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -709,6 +717,7 @@ __global__ void __launch_bounds__(256) tile_ranges(const uint32_t* tkey, const i
         for (int r = 0; r < 4; ++r) {
             const int64_t i = i0 + r;
             if (i >= K) break;
+            if (!LGS_CHECK(t[r] < n_tiles, 8, status)) break;
             if (i == 0 || prev != t[r]) ranges[t[r]].x = (uint32_t)i;
             const uint32_t next = r < 3 ? (i + 1 < K ? t[r + 1] : 0xffffffffu)
                                         : (i + 1 < K ? tkey[i + 1] : 0xffffffffu);
@@ -939,7 +948,7 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     }
     // 5. ranges (ka holds the sorted tile ids, va == vals)
     uint2* r2 = reinterpret_cast<uint2*>(ranges);
-    tile_ranges<<<152 * 4, 256, 0, s>>>(ka, d_status, capacity, r2);
+    tile_ranges<<<152 * 4, 256, 0, s>>>(ka, d_status, capacity, vs->n_tiles, r2);
     if (keys) write_keys<<<152 * 8, 256, 0, s>>>(ka, vals, pre->depth, d_status, capacity, keys);
     return cuda_status(cudaGetLastError());
 }
