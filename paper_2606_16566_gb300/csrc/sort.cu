@@ -459,12 +459,10 @@ __device__ __forceinline__ bool os_load(const OsSrc& src, int64_t i, uint32_t& k
         return true;
     }
     v = (uint32_t)i;
-    if (src.tiles[i] == 0u) {
-        k = 0xffffffffu;
-        return false;
-    }
-    k = __float_as_uint(src.depth[i]);
-    return true;
+    const uint32_t tiles = src.tiles[i];      // both loads issued together
+    const uint32_t bits = __float_as_uint(src.depth[i]);
+    k = tiles ? bits : 0xffffffffu;
+    return tiles != 0u;
 }
 
 // Per-digit-position histograms of the (kept) keys: ghist[p*256 + d] += count
