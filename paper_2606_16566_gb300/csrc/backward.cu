@@ -89,7 +89,7 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) render_bwd_localgs(BwdParams p, Views vs) {
+__global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views vs) {
     __shared__ float4 sV[BWD_BATCH];
     __shared__ float2 sDE[BWD_BATCH];
     __shared__ float4 sC[BWD_BATCH];

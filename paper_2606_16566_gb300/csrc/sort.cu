@@ -323,8 +323,9 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order, const 
     const bool valid = idx < m;
     const bool visible = idx < pass_count(mv, m);
     const uint32_t ent = visible ? order[idx] : 0u;
-    const bool live = visible && tiles[ent] != 0u;
-    const TightLane L = tight_lane_load(ent, live, rect, xy, conic, vs, n);
+    // the first entry pass kept only visible entries, so every entry before
+    // the visible count has a non-empty rect
+    const TightLane L = tight_lane_load(ent, visible, rect, xy, conic, vs, n);
     cnt[threadIdx.x] = 0u;
     __syncwarp();
     const uint32_t iw = warp_inclusive_sum(L.wd);
