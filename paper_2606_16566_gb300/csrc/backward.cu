@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
             }
             __syncwarp();
             {
+#pragma unroll 4
                 for (int i = nl - 1; i >= 0; --i) {
                     const int g = sLw[i];
                     const float4 V = sV[g];
