@@ -288,6 +288,7 @@ def run_batched(dev, steps):
     ms = float(np.mean(ts))
     P = lgs.n_pixels(cams)
     out = {"workload": "batched-3M-sh3-64-uneven-views-fwd+bwd-graph", "emission": "tight",
+           "view_groups": len(r.groups),
            "frames_s": len(cams) / (ms * 1e-3),
            "mpix_s": P / 1e6 / (ms * 1e-3), "ms_per_step": ms, "instances_K": int(st[2]),
            "tile": list(tune["tile"]), "persistent": tune["persistent"], "autotune": tune["timings"],
@@ -358,7 +359,8 @@ def run_indoor(dev, steps):
 
 def run_scale(dev, steps):
     """The scale scene: 30M SH3 Gaussians (256 clusters + background), 16 views
-    of 1920x1080 in one batch; forward with per-stage events, forward+backward
+    of 1920x1080 in one batch (view groups of at most 2^16 tiles); forward with
+    per-stage events, forward+backward
     as one graph replay, the warp-culled fraction of the Local-GS schedule, and
     the HBM rate of preprocess (algorithmic bytes: 236 B read per Gaussian,
     69 B written per (view, Gaussian) entry)."""
@@ -370,23 +372,19 @@ def run_scale(dev, steps):
     del sc
     n, V = g["means"].shape[0], len(cams)
     r = batch.Renderer(g, cams, backward=True, tight=True)
-    cfg_count = lgs.config(r.tile, "localgs", L.FLAG_TIGHT | L.FLAG_COUNT)
     r.forward()
-    lgs.render_fwd(r.pre, r.vals, r.ranges, cams, cfg_count, r.rgb, r.T, r.nc, r.status)
-    st = r.check()
-    pairs, cands = int(st[L.ST_PAIRS]), int(st[L.ST_CANDIDATES])
+    pairs, cands = r.count_pairs()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stage = []
     for i in range(max(3, steps // 8) + 1):
         flush.zero_()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
-        r.status.zero_()
-        lgs.preprocess(r.g, r.carr, r.cfg, out=r.pre, status=r.status)
+        r.stage_preprocess()
         e[1].record()
-        lgs.sort(r.pre, r.n, r.cams, r.cfg, r.capacity, None, r.vals, r.ranges, r.ws, r.status, with_keys=False)
+        r.stage_sort()
         e[2].record()
-        lgs.render_fwd(r.pre, r.vals, r.ranges, r.cams, r.cfg, r.rgb, r.T, r.nc, r.status)
+        r.stage_render()
         e[3].record()
         torch.cuda.synchronize()
         if i >= 1:
@@ -405,6 +403,7 @@ def run_scale(dev, steps):
            "mpix_s": P / 1e6 / (ms_f * 1e-3), "ms_per_step": ms_f,
            "stage_ms": {"preprocess": float(sm[0]), "sort": float(sm[1]), "render": float(sm[2])},
            "fwd_bwd": {"frames_s": V / (ms_fb * 1e-3), "ms_per_step": ms_fb, "replays": nrep},
+           "view_groups": len(r.groups),
            "instances_K": K, "culled_warp_fraction": 1.0 - pairs / 32.0 / max(cands, 1),
            "warp_candidates": cands, "pairs": pairs,
            "preprocess_hbm_gbs": pre_bytes / (sm[0] * 1e-3) / 1e9,

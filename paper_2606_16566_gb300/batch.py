@@ -30,9 +30,37 @@ from . import lgs
 TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
 
 
+MAX_GROUP_TILES = 1 << 16
+
+
+def view_groups(cams, tile, max_tiles=MAX_GROUP_TILES):
+    """Consecutive view groups [(v0, v1)] with at most max_tiles tiles (and at
+    most LGS_MAX_VIEWS views) each: inside a group tile ids fit in 16 bits, so
+    its tile-id sort takes two radix passes instead of three."""
+    tw, th = tile
+    groups, v0, acc = [], 0, 0
+    for v, c in enumerate(cams):
+        t = ((c["width"] + tw - 1) // tw) * ((c["height"] + th - 1) // th)
+        if v > v0 and (acc + t > max_tiles or v - v0 >= L.LGS_MAX_VIEWS):
+            groups.append((v0, v))
+            v0, acc = v, 0
+        acc += t
+    groups.append((v0, len(cams)))
+    return groups
+
+
 class Renderer:
+    """All buffers of the pipeline for a fixed camera set, eager or as one
+    CUDA graph. Views are processed in groups of at most MAX_GROUP_TILES tiles
+    (one group for most batches): one preprocess call for all views, then a
+    sort, render and adjoint call per group on that group's rows of the
+    preprocess outputs, pixels and 2D gradients (so a group's lists hold
+    indices into its own rows; lists() gives the global form). A tile's list
+    depends only on the entries of its own view, so grouping changes no
+    output."""
+
     def __init__(self, g, cams, tile=(16, 16), mode="localgs", persistent=False, capacity=None,
-                 headroom=1.10, backward=False, tight=False):
+                 headroom=1.10, backward=False, tight=False, max_group_tiles=MAX_GROUP_TILES):
         self.g, self.cams, self.tile, self.mode = g, cams, tuple(tile), mode
         flags = (L.FLAG_PERSISTENT if persistent else 0) | (L.FLAG_TIGHT if tight else 0)
         self.cfg = lgs.config(tile, mode, flags)
@@ -40,17 +68,21 @@ class Renderer:
         dev = g["means"].device
         self.n = g["means"].shape[0]
         self.m = max(self.n * len(cams), 1)
+        self.groups = view_groups(cams, self.tile, max_group_tiles)
         if capacity is None:
-            probe = lgs.render(g, cams, tile=tile, mode=mode, flags=L.FLAG_TIGHT if tight else 0)
-            capacity = int(math.ceil(probe["K"] * headroom)) + 1024
-            del probe
-        self.capacity = capacity
-        self.status = lgs.new_status(dev)
+            caps = []
+            for v0, v1 in self.groups:
+                probe = lgs.render(g, cams[v0:v1], tile=tile, mode=mode, flags=L.FLAG_TIGHT if tight else 0)
+                caps.append(int(math.ceil(probe["K"] * headroom)) + 1024)
+                del probe
+        else:
+            caps = [int(capacity)] * len(self.groups) if len(self.groups) == 1 else list(capacity)
+        self.capacity = sum(caps)
         self.pre = lgs.PreOut.empty(self.m, dev)
-        self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
         self.ranges = torch.empty((lgs.n_tiles(cams, self.cfg), 2), dtype=torch.int32, device=dev)
-        self.ws = torch.empty(lgs.sort_workspace_size(self.n * len(cams), capacity), dtype=torch.uint8,
-                              device=dev)
+        self.ws = torch.empty(max(lgs.sort_workspace_size(self.n * (v1 - v0), c)
+                                  for (v0, v1), c in zip(self.groups, caps)), dtype=torch.uint8, device=dev)
         P = lgs.n_pixels(cams)
         self.rgb = torch.empty(3 * P, dtype=torch.float32, device=dev)
         self.T = torch.empty(P, dtype=torch.float32, device=dev)
@@ -60,22 +92,65 @@ class Renderer:
             self.d_rgb = torch.zeros(3 * P, dtype=torch.float32, device=dev)
             self.d_T = None
             self.grads = lgs.new_grads(g, len(cams))
+        # per-group views of the buffers
+        self.parts = []
+        voff = toff = poff = 0
+        for (v0, v1), cap in zip(self.groups, caps):
+            cg = cams[v0:v1]
+            nt, npx = lgs.n_tiles(cg, self.cfg), lgs.n_pixels(cg)
+            part = {"cams": cg, "carr": lgs.cameras(cg), "cap": cap, "voff": voff, "toff": toff,
+                    "pre": self.pre.rows(v0 * self.n, v1 * self.n), "vals": self.vals[voff:voff + cap],
+                    "ranges": self.ranges[toff:toff + nt], "rgb": self.rgb[3 * poff:3 * (poff + npx)],
+                    "T": self.T[poff:poff + npx], "nc": self.nc[poff:poff + npx],
+                    "status": lgs.new_status(dev)}
+            if backward:
+                part["d_rgb"] = self.d_rgb[3 * poff:3 * (poff + npx)]
+                part["grads"] = dict(self.grads)
+                for k, w in (("xy2d", 2), ("conic2d", 4), ("rgb2d", 3)):
+                    part["grads"][k] = self.grads[k][v0 * self.n:v1 * self.n]
+            self.parts.append(part)
+            voff, toff, poff = voff + cap, toff + nt, poff + npx
+        self.status = self.parts[0]["status"]
         self.graph = None
 
     # ------------------------------------------------------------------ eager
-    def forward(self, stream=None):
-        self.status.zero_()
+    def stage_preprocess(self, stream=None):
+        for q in self.parts:
+            q["status"].zero_()
         lgs.preprocess(self.g, self.carr, self.cfg, out=self.pre, status=self.status, stream=stream)
-        lgs.sort(self.pre, self.n, self.cams, self.cfg, self.capacity, None, self.vals, self.ranges,
-                 self.ws, self.status, stream=stream, with_keys=False)
-        lgs.render_fwd(self.pre, self.vals, self.ranges, self.cams, self.cfg, self.rgb, self.T, self.nc,
-                       self.status, stream=stream)
+
+    def stage_sort(self, stream=None):
+        for q in self.parts:
+            lgs.sort(q["pre"], self.n, q["cams"], self.cfg, q["cap"], None, q["vals"], q["ranges"],
+                     self.ws, q["status"], stream=stream, with_keys=False)
+
+    def stage_render(self, cfg=None, stream=None):
+        for q in self.parts:
+            lgs.render_fwd(q["pre"], q["vals"], q["ranges"], q["cams"], cfg or self.cfg, q["rgb"], q["T"],
+                           q["nc"], q["status"], stream=stream)
+
+    def forward(self, stream=None):
+        self.stage_preprocess(stream)
+        self.stage_sort(stream)
+        self.stage_render(stream=stream)
+
+    def count_pairs(self):
+        """(pixel-Gaussian pairs, warp candidates) of the Local-GS schedule over
+        all groups (an extra render with LGS_FLAG_COUNT after a forward)."""
+        cfg = lgs.config(self.tile, self.mode, self.cfg.flags | L.FLAG_COUNT)
+        for q in self.parts:
+            q["status"][L.ST_PAIRS] = 0
+            q["status"][L.ST_CANDIDATES] = 0
+        self.stage_render(cfg)
+        st = self.check()
+        return int(st[L.ST_PAIRS]), int(st[L.ST_CANDIDATES])
 
     def backward(self, stream=None):
         for k in ("means", "scales", "quats", "opacities", "sh"):
             self.grads[k].zero_()
-        lgs.render_bwd(self.g, self.cams, self.cfg, self.pre, self.vals, self.ranges, self.T, self.nc,
-                       self.d_rgb, self.d_T, self.grads, self.status, stream=stream)
+        for q in self.parts:
+            lgs.render_bwd(self.g, q["cams"], self.cfg, q["pre"], q["vals"], q["ranges"], q["T"], q["nc"],
+                           q["d_rgb"], self.d_T, q["grads"], q["status"], stream=stream)
 
     def step(self):
         if self.graph is not None:
@@ -105,11 +180,32 @@ class Renderer:
         return self
 
     def check(self):
-        """Reads the device status; raises on a device-side error."""
-        st = lgs.read_status(self.status)
-        if st[L.ST_CODE] != 0:
-            raise L.LgsError(int(st[L.ST_CODE]), f"device status (detail {int(st[L.ST_DETAIL])})")
-        return st
+        """Reads the device status of every group; raises on a device-side
+        error. Returns the status words with the instance counts summed."""
+        total = None
+        for q in self.parts:
+            st = lgs.read_status(q["status"])
+            if st[L.ST_CODE] != 0:
+                raise L.LgsError(int(st[L.ST_CODE]), f"device status (detail {int(st[L.ST_DETAIL])})")
+            if total is None:
+                total = st.copy()
+            else:
+                for w in (L.ST_NUM_INSTANCES, L.ST_NONFINITE, L.ST_PAIRS, L.ST_CANDIDATES):
+                    total[w] += st[w]
+        return total
+
+    def lists(self):
+        """(vals, ranges) of all groups as one list set: ranges index vals and
+        vals are entry indices v*N + i over all views (a group's own lists hold
+        indices into its own rows of the preprocess outputs)."""
+        ranges = self.ranges.clone()
+        vals = self.vals.clone()
+        for (v0, _), q in zip(self.groups, self.parts):
+            r = ranges[q["toff"]:q["toff"] + q["ranges"].shape[0]]
+            nonempty = r[:, 1] > r[:, 0]
+            r[nonempty] += q["voff"]
+            vals[q["voff"]:q["voff"] + q["cap"]] += v0 * self.n
+        return vals, ranges
 
     def images(self):
         return lgs.split_views(self.rgb, self.cams, 3)

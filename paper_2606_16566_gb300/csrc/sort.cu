@@ -310,7 +310,7 @@ __device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t e) {
 // instances that emission will write for entry order[j] (0 past the visible
 // entries).
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) count_tight(const uint32_t* order, const uint32_t* tiles,
+__global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
                                                    const uint64_t* rect, const float4* xy,
                                                    const float4* conic, int64_t m, const int64_t* mv,
                                                    int64_t n, Views vs, uint32_t* tiles_sorted) {
@@ -900,13 +900,13 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     if (!tight)
         gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
     else if (vs->tile_w == 16)
-        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
                                                ws->tiles_s);
     else if (vs->tile_w == 8)
-        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
                                               ws->tiles_s);
     else
-        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->tiles, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
                                               ws->tiles_s);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);

@@ -99,6 +99,11 @@ class PreOut:
                       torch.empty(m, dtype=torch.int64, **f),
                       torch.empty(m, dtype=torch.uint8, **f))
 
+    def rows(self, a, b) -> "PreOut":
+        """The entries a..b-1 (e.g. the views of a group), as views of the same memory."""
+        return PreOut(*(t[a:b] for t in (self.xy, self.conic, self.rgb, self.depth, self.radius,
+                                          self.tiles, self.rect, self.flags)))
+
     def struct(self) -> L.lgs_pre_out:
         return L.lgs_pre_out(*(t.data_ptr() for t in (self.xy, self.conic, self.rgb, self.depth,
                                                          self.radius, self.tiles, self.rect,

@@ -89,9 +89,11 @@ def test_batched_64_uneven_views_graph_fwd_bwd():
     torch.cuda.synchronize()
     st = r.check()
     assert st[2] > 0
+    vals, ranges = r.lists()
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
-           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": r.vals, "ranges": r.ranges}
+           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
     n = sc["means"].shape[0]
+    assert len(r.groups) > 1
     for v in (0, 37):
         view = to_numpy_view(res, v, cams, n, (16, 16))
         rep, _ = full_view_parity(sc, cams[v], view, (16, 16))
@@ -100,3 +102,34 @@ def test_batched_64_uneven_views_graph_fwd_bwd():
         assert_image_parity(rep, f"batched view {v}")
     for k in ("means", "scales", "quats", "opacities", "sh"):
         assert torch.isfinite(r.grads[k]).all(), k
+
+
+def test_view_groups_change_no_output():
+    """Groups of at most two views (tiny max_group_tiles) against one group:
+    identical images, final T, contributor counts and tile lists; gradients
+    equal up to the order of float atomics."""
+    sc, _ = scenes.outdoor(n=30000)
+    cams = _uneven_views(5, seed=6)
+    g = lgs.to_device(sc)
+    one = batch.Renderer(g, cams, backward=True, tight=True)
+    many = batch.Renderer(g, cams, backward=True, tight=True, max_group_tiles=300)
+    assert len(one.groups) == 1 and len(many.groups) >= 3
+    for r in (one, many):
+        r.d_rgb.copy_(torch.linspace(-1, 1, r.d_rgb.numel(), device="cuda"))
+        r.forward()
+        r.backward()
+    torch.cuda.synchronize()
+    assert one.check()[2] == many.check()[2]
+    for a, b in ((one.rgb, many.rgb), (one.T, many.T), (one.nc, many.nc)):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+    va, ra = one.lists()
+    vb, rb = many.lists()
+    ra, rb = ra.cpu().numpy(), rb.cpu().numpy()
+    va, vb = va.cpu().numpy(), vb.cpu().numpy()
+    for t in range(ra.shape[0]):
+        assert np.array_equal(va[ra[t, 0]:ra[t, 1]], vb[rb[t, 0]:rb[t, 1]]), t
+    # the 3D gradients accumulate over one call per group, so float atomics sum
+    # in another order (quaternion gradients cancel the most)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        d = (one.grads[k] - many.grads[k]).norm() / one.grads[k].norm().clamp_min(1e-30)
+        assert d.item() <= 1e-4, k

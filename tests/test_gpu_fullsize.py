@@ -41,8 +41,9 @@ def test_indoor_training_step():
     for k in ("means", "scales", "quats", "opacities", "sh"):
         assert torch.isfinite(r.grads[k]).all(), k
         assert r.grads[k].abs().sum().item() > 0, k
+    vals, ranges = r.lists()
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
-           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": r.vals, "ranges": r.ranges}
+           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
     _check_sampled(sc, cams, res, 0, 0.05, seed=11)
 
 
@@ -120,6 +121,7 @@ def test_scale_30M_sampled_view():
     r.forward()
     torch.cuda.synchronize()
     r.check()
+    vals, ranges = r.lists()
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
-           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": r.vals, "ranges": r.ranges}
+           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
     _check_sampled(sc, cams, res, 1, 0.04, seed=12)
