@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-scale", action="store_true", help="skip the 30M-Gaussian scale scene")
     p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
     p.add_argument("--tight", action="store_true", help="with --profile: tight-box emission")
+    p.add_argument("--scene", default="outdoor", choices=["outdoor", "indoor", "scale"],
+                   help="with --profile: the scene (indoor and scale run through batch.Renderer)")
     return p.parse_args()
 
 
@@ -422,6 +424,22 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     tile = tuple(int(x) for x in args.tile.split("x"))
+    if args.profile and args.scene != "outdoor":
+        from paper_2606_16566_gb300 import batch
+        scene, cams = getattr(scenes, args.scene)()
+        cams = cams[:args.views]
+        g = lgs.to_device(scene, dev)
+        del scene
+        r = batch.Renderer(g, cams, tile=tile, mode=args.mode, backward=args.backward, tight=args.tight)
+        if args.backward:
+            r.d_rgb.fill_(1.0 / r.d_rgb.numel())
+        for _ in range(args.warmup + args.steps):
+            r.forward()
+            if args.backward:
+                r.backward()
+        torch.cuda.synchronize()
+        r.check()
+        return
     scene, cams = scenes.outdoor()
     cams = cams[:args.views]
     g = lgs.to_device(scene, dev)
