@@ -75,14 +75,17 @@ def test_autotune_picks_a_measured_candidate(tmp_path):
     assert again["cached"] and tuple(again["tile"]) == tuple(res["tile"])
 
 
-def test_batched_64_uneven_views_graph_fwd_bwd():
+@pytest.mark.parametrize("tile,persistent,tight", [((16, 16), True, False), ((8, 32), False, True)])
+def test_batched_64_uneven_views_graph_fwd_bwd(tile, persistent, tight):
     """The batched workload: 3M clustered SH3 Gaussians, 64 cameras of uneven
     resolution (800..1920 x 800..1080), forward + backward captured in one CUDA
-    graph with the persistent render; two views checked against the oracle."""
+    graph (view groups of at most 2^16 tiles); two views checked against the
+    oracle. The second case is the benchmark's launch (tight-box emission, the
+    8x32 tile its autotuner picks on this workload, one CTA per tile)."""
     sc, cams = scenes.batched()
     assert len(cams) == 64
     g = lgs.to_device(sc)
-    r = batch.Renderer(g, cams, persistent=True, backward=True)
+    r = batch.Renderer(g, cams, tile=tile, persistent=persistent, backward=True, tight=tight)
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
     r.step()
@@ -95,8 +98,8 @@ def test_batched_64_uneven_views_graph_fwd_bwd():
     n = sc["means"].shape[0]
     assert len(r.groups) > 1
     for v in (0, 37):
-        view = to_numpy_view(res, v, cams, n, (16, 16))
-        rep, _ = full_view_parity(sc, cams[v], view, (16, 16))
+        view = to_numpy_view(res, v, cams, n, tile)
+        rep, _ = full_view_parity(sc, cams[v], view, tile, tight=tight)
         print(v, rep)
         assert not rep["unexplained_tiles"], rep["unexplained_tiles"][:10]
         assert_image_parity(rep, f"batched view {v}")

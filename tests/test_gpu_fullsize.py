@@ -15,21 +15,23 @@ from parity import assert_image_parity, full_view_parity, sample_tiles, to_numpy
 pytestmark = pytest.mark.gpu
 
 
-def _check_sampled(sc, cams, res, v, frac, seed):
+def _check_sampled(sc, cams, res, v, frac, seed, tile=(16, 16), tight=False):
     n = sc["means"].shape[0]
-    mask = sample_tiles(cams[v], frac, seed)
-    view = to_numpy_view(res, v, cams, n, (16, 16))
-    rep, _ = full_view_parity(sc, cams[v], view, (16, 16), tile_mask=mask)
+    mask = sample_tiles(cams[v], frac, seed, tile)
+    view = to_numpy_view(res, v, cams, n, tile)
+    rep, _ = full_view_parity(sc, cams[v], view, tile, tile_mask=mask, tight=tight)
     print(v, rep)
     assert not rep["unexplained_tiles"], rep["unexplained_tiles"][:10]
     assert_image_parity(rep, f"view {v}")
 
 
-def test_indoor_training_step():
-    """Forward + L1 loss against a seeded random target + full adjoint."""
+@pytest.mark.parametrize("tight", [False, True])
+def test_indoor_training_step(tight):
+    """Forward + L1 loss against a seeded random target + full adjoint (the
+    benchmark's indoor step uses tight-box emission)."""
     sc, cams = scenes.indoor()
     g = lgs.to_device(sc)
-    r = batch.Renderer(g, cams, backward=True)
+    r = batch.Renderer(g, cams, backward=True, tight=tight)
     r.forward()
     target = torch.rand(r.rgb.shape, generator=torch.Generator(device="cuda").manual_seed(7), device="cuda")
     loss = (r.rgb - target).abs().mean()
@@ -44,7 +46,7 @@ def test_indoor_training_step():
     vals, ranges = r.lists()
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
            "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
-    _check_sampled(sc, cams, res, 0, 0.05, seed=11)
+    _check_sampled(sc, cams, res, 0, 0.05, seed=11, tight=tight)
 
 
 def _indoor_crop(n_keep=2000, win=128):
@@ -125,3 +127,21 @@ def test_scale_30M_sampled_view():
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
            "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
     _check_sampled(sc, cams, res, 1, 0.04, seed=12)
+
+
+def test_scale_30M_bench_configuration():
+    """The benchmark's scale configuration: all 16 views of 1920x1080 in one
+    Renderer with tight-box emission (two view groups of 8); two views, one
+    per group, checked on sampled tiles."""
+    sc, cams = scenes.scale()
+    g = lgs.to_device(sc)
+    r = batch.Renderer(g, cams, tight=True)
+    assert len(r.groups) == 2
+    r.forward()
+    torch.cuda.synchronize()
+    r.check()
+    vals, ranges = r.lists()
+    res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
+           "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
+    for v, seed in ((5, 13), (12, 14)):
+        _check_sampled(sc, cams, res, v, 0.02, seed=seed, tight=True)
