@@ -42,7 +42,9 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--tile", default="16x16")
+    p.add_argument("--tile", default="auto",
+                   help="tile shape WxH, or auto: the autotuner's pick for the Local-GS forward "
+                        "(with --profile, auto means 16x16)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--profile", action="store_true",
@@ -423,7 +425,7 @@ def run_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
     if args.profile and args.scene != "outdoor":
         from paper_2606_16566_gb300 import batch
         scene, cams = getattr(scenes, args.scene)()
@@ -457,33 +459,51 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         return
     TF = L.FLAG_TIGHT
-    variants = {"localgs": lgs.config(tile, "localgs"), "plain": lgs.config(tile, "plain"),
-                "localgs_tight": lgs.config(tile, "localgs", TF), "plain_tight": lgs.config(tile, "plain", TF),
+    tuned = None
+    persistent = 0
+    if args.tile == "auto":
+        # tile shape and launch of the Local-GS forward from the project's
+        # autotuner (timed graph replays of every candidate, outside the timed region)
+        from paper_2606_16566_gb300 import batch
+        tuned = batch.autotune(g, cams, tight=True, reps=5, use_cache=False)
+        tile = tuple(tuned["tile"])
+        persistent = L.FLAG_PERSISTENT if tuned["persistent"] else 0
+    PF = persistent
+    # the plain rasterizer runs on the standard 3DGS 16x16 tile, its own best
+    # shape; the Local-GS variants on the tuned one
+    tile_p = (16, 16) if args.tile == "auto" else tile
+    variants = {"localgs": lgs.config(tile, "localgs", PF), "plain": lgs.config(tile_p, "plain"),
+                "localgs_tight": lgs.config(tile, "localgs", TF | PF), "plain_tight": lgs.config(tile_p, "plain", TF),
                 "literal_tight": lgs.config(tile, "literal", TF)}
     forward_only = {"literal_tight"}       # the paper-literal study variant has no adjoint
     mode_of = {L.MODE_LOCALGS: "localgs", L.MODE_PLAIN: "plain", L.MODE_LITERAL: "literal"}
 
-    # discover K and size the instance buffers once (outside the timed region)
-    probe = lgs.render(g, cams, tile=tile)
-    K = probe["K"]
-    pipe = Pipeline(g, cams, tile, int(K * 1.05) + 1024)
-    del probe
+    # discover K and size the instance buffers once per tile shape (outside the timed region)
+    pipes_by_tile = {}
+    for t in {tile, tile_p}:
+        probe = lgs.render(g, cams, tile=t)
+        pipes_by_tile[t] = Pipeline(g, cams, t, int(probe["K"] * 1.05) + 1024)
+        del probe
+    pipe = pipes_by_tile[tile]
+    pipe_of = {name: pipes_by_tile[(cfg.tile_w, cfg.tile_h)] for name, cfg in variants.items()}
     # schedule work of the Local-GS render (pixel-Gaussian pairs) and K, counted once
     counts = {}
     for name, cfg in variants.items():
-        pipe.step(lgs.config(tile, mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT))
-        st = lgs.read_status(pipe.status)
+        q = pipe_of[name]
+        q.step(lgs.config((cfg.tile_w, cfg.tile_h), mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT))
+        st = lgs.read_status(q.status)
         if st[L.ST_CODE] != 0:
             raise L.LgsError(int(st[L.ST_CODE]), f"device status in {name}")
         counts[name] = {"pairs": int(st[L.ST_PAIRS]), "K": int(st[L.ST_NUM_INSTANCES])}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    pipe.setup_backward()
+    for q in pipes_by_tile.values():
+        q.setup_backward()
     for _ in range(args.warmup):
         for name, cfg in variants.items():
-            pipe.step(cfg)
+            pipe_of[name].step(cfg)
             if name not in forward_only:
-                pipe.stage_backward(cfg)
+                pipe_of[name].stage_backward(cfg)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -491,15 +511,16 @@ def run_ours(args, rank, world):
     fwd, fb = {}, {}
     with Clocks(dev.index) as clk:
         for name, cfg in variants.items():
-            fwd[name] = time_steps(pipe, cfg, args.steps, flush)
+            fwd[name] = time_steps(pipe_of[name], cfg, args.steps, flush)
             if name not in forward_only:
-                fb[name] = time_steps(pipe, cfg, n_bw, flush, backward=True)
+                fb[name] = time_steps(pipe_of[name], cfg, n_bw, flush, backward=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    st = lgs.read_status(pipe.status)
-    if st[L.ST_CODE] != 0:
-        raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
+    for q in pipes_by_tile.values():
+        st = lgs.read_status(q.status)
+        if st[L.ST_CODE] != 0:
+            raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
     ms = {n: float(fwd[n].sum(1).mean()) for n in variants}
     ms_b = {n: float(fb[n].sum(1).mean()) for n in fb}
     if world > 1:
@@ -612,7 +633,10 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n, "tile": args.tile,
+        "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n,
+                   "tile": f"{tile[0]}x{tile[1]}", "persistent": bool(persistent),
+                   "tile_choice": "autotuned" if tuned else "fixed",
+                   "plain_tile": f"{tile_p[0]}x{tile_p[1]}",
                    "emission": emission, "instances_K": counts[head]["K"],
                    "l2": "flushed between steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
@@ -623,12 +647,15 @@ def run_ours(args, rank, world):
         "render_speedup_vs_plain": float(fwd[plain_same].mean(0)[2]) / render_ms,
         "variants": {n: summary(n) for n in variants},
         "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step",
-        "roofline": {"bound": "alu", "kernel": "render_localgs", "achieved": achieved, "peak": peak,
+        "autotune": tuned["timings"] if tuned else None,
+        "roofline": {"bound": "alu", "kernel": "render_localgs" + ("_persistent" if persistent else ""), "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic("render_localgs_16x16_" + emission),
+                     "traffic": recorded_traffic(f"render_localgs{'_persistent' if persistent else ''}"
+                                                 f"_{tile[0]}x{tile[1]}_{emission}"),
                      "work": f"{counts[head]['pairs']} pixel-Gaussian pairs x 19 FP32 flops",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)"},
-        "gpu_launches": len(variants) * pipe.launches() * args.steps + len(fb) * (pipe.launches() + 2) * n_bw,
+        "gpu_launches": sum(pipe_of[n].launches() * args.steps for n in variants)
+                        + sum((pipe_of[n].launches() + 2) * n_bw for n in fb),
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched": batched,

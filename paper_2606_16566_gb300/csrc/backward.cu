@@ -191,32 +191,29 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
                     if (!__any_sync(0xffffffffu, contrib)) continue;   // nothing to reduce
                     const float e2 = ex2_approx_b(pw);
                     const float al = fminf(0.99f, e2);
+                    // branch-free: lanes that do not contribute get alpha 0, which
+                    // leaves T and the accumulated colour exactly as they were
                     float v[8];
-                    float gb = 0.f;
-                    if (contrib) {
-                        const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
-                        const float Tk = T * inv;
-                        const float w = al * Tk;
-                        v[5] = w * g0;
-                        v[6] = w * g1;
-                        gb = w * g2;
-                        const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
-                        const float dal = Tk * cg - tail * inv;
-                        A0 = fmaf(al, col.x - A0, A0);
-                        A1 = fmaf(al, col.y - A1, A1);
-                        A2 = fmaf(al, col.z - A2, A2);
-                        T = Tk;
-                        const float dp = (e2 > 0.99f) ? 0.f : dal * al;   // natural-log power
-                        v[0] = dp * bx2;
-                        v[1] = dp * bxy;
-                        v[2] = dp * by2;
-                        v[3] = dp * xl;
-                        v[4] = dp * yl;
-                        v[7] = dp;
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] = 0.f;
-                    }
+                    const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
+                    const float Tk = T * inv;
+                    const float ac = contrib ? al : 0.f;
+                    const float w = ac * Tk;
+                    v[5] = w * g0;
+                    v[6] = w * g1;
+                    const float gb = w * g2;
+                    const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
+                    const float dal = Tk * cg - tail * inv;
+                    A0 = fmaf(ac, col.x - A0, A0);
+                    A1 = fmaf(ac, col.y - A1, A1);
+                    A2 = fmaf(ac, col.z - A2, A2);
+                    T = contrib ? Tk : T;
+                    const float dp = (contrib && !(e2 > 0.99f)) ? dal * al : 0.f;
+                    v[0] = dp * bx2;
+                    v[1] = dp * bxy;
+                    v[2] = dp * by2;
+                    v[3] = dp * xl;
+                    v[4] = dp * yl;
+                    v[7] = dp;
                     const float s8 = warp_sum8_transposed(v);
                     const float s9 = warp_sum(gb);
                     if ((lane & 3) == 0) atomicAdd(&sG[g][lane >> 2], s8);
