@@ -5,8 +5,11 @@
 // render_bwd_localgs: one CTA per tile, the tile list walked back to front from
 // the largest contributor count in the tile. Gaussians are staged and hoisted
 // exactly as in the forward kernel (same V, same warp mask, same FP32
-// arithmetic), so every alpha >= 1/255 decision is reproduced bit for bit; a
-// lane takes part for list positions <= its stored n_contrib. Per pixel the
+// arithmetic), so every alpha >= 1/255 decision is reproduced bit for bit. Each
+// warp compacts its list of the batch (set mask bits up to its largest
+// contributor count) and walks it back to front; a lane takes part for list
+// positions <= its stored n_contrib, the others get alpha 0 (branch-free), and
+// a warp with no contributing lane skips the reduction after one vote. Per pixel the
 // transmittance before each Gaussian is recovered as T / (1 - alpha) from the
 // stored final T, and
 //   dL/drgb_k  = alpha_k T_k g

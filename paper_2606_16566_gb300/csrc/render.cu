@@ -2,8 +2,9 @@
 // blending (Local-GS Sec. II-A render kernel).
 //
 // render_localgs implements the three Local-GS stages (Sec. III):
-//  (1) hoisting (Sec. III-B): while a batch of the tile's Gaussians is staged
-//      into shared memory, each staging thread maps (a, b, c, ln o) and the
+//  (1) hoisting (Sec. III-B): a batch of the tile's Gaussians is staged into
+//      shared memory (their xy, conic and rgb records copied with cp.async one
+//      batch ahead of the blend); each staging thread maps (a, b, c, ln o) and the
 //      tile-local offset Delta to the six coefficients V = [A..F] of
 //      ln(alpha) = A x'^2 + B x'y' + C y'^2 + D x' + E y' + F (Eq. hoist
 //      transform), scaled by log2(e) so that alpha = 2^(V . B_local) is one
@@ -17,7 +18,8 @@
 //      its vertical span into an 8-bit mask of warp strips. Each warp then
 //      compacts the batch into its own index list (one __ballot_sync per 32
 //      candidates, written to shared memory) and walks that list with a plain
-//      counter, so culled Gaussians cost no issue slot in the blend loop.
+//      counter (unrolled by 4), so culled Gaussians cost no issue slot in the
+//      blend loop.
 //  (3) warp-coherent blending (Sec. III-D): the per-pair data path is a fixed
 //      branch-free sequence (5 FMA dot product, ex2, clamp, predicated
 //      threshold/stop, w = alpha T, 3 FMA colour, 1 FMA transmittance); the
