@@ -157,6 +157,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_max_over_ranks(values, world, device=None):
+    """The element-wise maximum of per-rank timings over all ranks (identity on
+    one rank): the slowest rank decides a step's time."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 # ---------------------------------------------------------------- GPU arm
 class Pipeline:
     """Preallocated buffers for repeated batched frames through the C ABI."""
@@ -523,13 +535,10 @@ def run_ours(args, rank, world):
             raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
     ms = {n: float(fwd[n].sum(1).mean()) for n in variants}
     ms_b = {n: float(fb[n].sum(1).mean()) for n in fb}
-    if world > 1:
-        names, names_b = list(ms), list(ms_b)
-        t = torch.tensor([ms[n] for n in names] + [ms_b[n] for n in names_b], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        vals = t.tolist()
-        ms = dict(zip(names, vals[:len(names)]))
-        ms_b = dict(zip(names_b, vals[len(names):]))
+    names, names_b = list(ms), list(ms_b)
+    vals = reduce_max_over_ranks([ms[n] for n in names] + [ms_b[n] for n in names_b], world, dev)
+    ms = dict(zip(names, vals[:len(names)]))
+    ms_b = dict(zip(names_b, vals[len(names):]))
     views = len(cams)
     P = lgs.n_pixels(cams)
     # headline: the faster of the two Local-GS emissions (both reported)
@@ -611,10 +620,7 @@ def run_ours(args, rank, world):
             st = lgs.read_status(q.status)
             if st[L.ST_CODE] != 0:
                 raise L.LgsError(int(st[L.ST_CODE]), "device status in the end-to-end steps")
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = t.item()
+        ms_e2e = reduce_max_over_ranks([ms_e2e], world, dev)[0]
         e2e = {"value": world * views / (ms_e2e * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                "schedule": "2 buffer sets, upload / render / download of consecutive steps on 3 streams"}
