@@ -286,7 +286,8 @@ def run_batched(dev, steps):
     g = lgs.to_device(sc, dev)
     del sc
     tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False, tight=True)
-    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True, tight=True)
+    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True, tight=True,
+                       batch=tune["batch"])
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -307,7 +308,8 @@ def run_batched(dev, steps):
            "view_groups": len(r.groups),
            "frames_s": len(cams) / (ms * 1e-3),
            "mpix_s": P / 1e6 / (ms * 1e-3), "ms_per_step": ms, "instances_K": int(st[2]),
-           "tile": list(tune["tile"]), "persistent": tune["persistent"], "autotune": tune["timings"],
+           "tile": list(tune["tile"]), "persistent": tune["persistent"], "staging_batch": tune["batch"],
+           "autotune": tune["timings"],
            "replays": len(ts)}
     del r, g
     torch.cuda.empty_cache()
@@ -480,13 +482,14 @@ def run_ours(args, rank, world):
         tuned = batch.autotune(g, cams, tight=True, reps=5, use_cache=False)
         tile = tuple(tuned["tile"])
         persistent = L.FLAG_PERSISTENT if tuned["persistent"] else 0
+    nbat = tuned["batch"] if tuned else 0
     PF = persistent
     # the plain rasterizer runs on the standard 3DGS 16x16 tile, its own best
     # shape; the Local-GS variants on the tuned one
     tile_p = (16, 16) if args.tile == "auto" else tile
-    variants = {"localgs": lgs.config(tile, "localgs", PF), "plain": lgs.config(tile_p, "plain"),
-                "localgs_tight": lgs.config(tile, "localgs", TF | PF), "plain_tight": lgs.config(tile_p, "plain", TF),
-                "literal_tight": lgs.config(tile, "literal", TF)}
+    variants = {"localgs": lgs.config(tile, "localgs", PF, nbat), "plain": lgs.config(tile_p, "plain"),
+                "localgs_tight": lgs.config(tile, "localgs", TF | PF, nbat),
+                "plain_tight": lgs.config(tile_p, "plain", TF), "literal_tight": lgs.config(tile, "literal", TF)}
     forward_only = {"literal_tight"}       # the paper-literal study variant has no adjoint
     mode_of = {L.MODE_LOCALGS: "localgs", L.MODE_PLAIN: "plain", L.MODE_LITERAL: "literal"}
 
@@ -502,7 +505,7 @@ def run_ours(args, rank, world):
     counts = {}
     for name, cfg in variants.items():
         q = pipe_of[name]
-        q.step(lgs.config((cfg.tile_w, cfg.tile_h), mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT))
+        q.step(lgs.config((cfg.tile_w, cfg.tile_h), mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT, cfg.batch))
         st = lgs.read_status(q.status)
         if st[L.ST_CODE] != 0:
             raise L.LgsError(int(st[L.ST_CODE]), f"device status in {name}")
@@ -641,6 +644,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n,
                    "tile": f"{tile[0]}x{tile[1]}", "persistent": bool(persistent),
+                   "staging_batch": nbat or 256,
                    "tile_choice": "autotuned" if tuned else "fixed",
                    "plain_tile": f"{tile_p[0]}x{tile_p[1]}",
                    "emission": emission, "instances_K": counts[head]["K"],

@@ -136,8 +136,10 @@ typedef struct {
 #define LGS_FLAG_TIGHT 4
 
 /* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}; 8 warps per tile, each a
- * tile_w x tile_h/8 strip), render mode and flags. batch = Gaussians staged in
- * shared memory per round (0 = 256; 64, 128 or 256). */
+ * tile_w x tile_h/8 strip), render mode and flags. batch = Gaussians the
+ * Local-GS render (LGS_MODE_LOCALGS) stages in shared memory per round: 0
+ * (= 256), 64, 128 or 256, else LGS_ERR_UNSUPPORTED; the results do not depend
+ * on it. The other modes and the adjoint stage 256. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t mode;

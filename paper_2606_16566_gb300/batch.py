@@ -11,9 +11,10 @@ tensors and the upstream gradient are read in place, so they may change
 between replays.
 
 ``autotune`` times the candidate tile shapes (16x16, 8x32, 32x8: the warp
-strip of a 256-thread tile is 16x2, 8x4 or 32x1 pixels) with and without the
-persistent render launch on the actual workload and caches the fastest per
-(Gaussian-count bucket, pixel-count bucket, view count, mode).
+strip of a 256-thread tile is 16x2, 8x4 or 32x1 pixels), with and without the
+persistent render launch and with staging batches of 256 or 128 Gaussians, on
+the actual workload, and caches the fastest per (Gaussian-count bucket,
+pixel-count bucket, view count, mode, emission).
 """
 from __future__ import annotations
 
@@ -60,10 +61,10 @@ class Renderer:
     output."""
 
     def __init__(self, g, cams, tile=(16, 16), mode="localgs", persistent=False, capacity=None,
-                 headroom=1.10, backward=False, tight=False, max_group_tiles=MAX_GROUP_TILES):
+                 headroom=1.10, backward=False, tight=False, max_group_tiles=MAX_GROUP_TILES, batch=0):
         self.g, self.cams, self.tile, self.mode = g, cams, tuple(tile), mode
         flags = (L.FLAG_PERSISTENT if persistent else 0) | (L.FLAG_TIGHT if tight else 0)
-        self.cfg = lgs.config(tile, mode, flags)
+        self.cfg = lgs.config(tile, mode, flags, batch)
         self.carr = lgs.cameras(cams)
         dev = g["means"].device
         self.n = g["means"].shape[0]
@@ -137,7 +138,7 @@ class Renderer:
     def count_pairs(self):
         """(pixel-Gaussian pairs, warp candidates) of the Local-GS schedule over
         all groups (an extra render with LGS_FLAG_COUNT after a forward)."""
-        cfg = lgs.config(self.tile, self.mode, self.cfg.flags | L.FLAG_COUNT)
+        cfg = lgs.config(self.tile, self.mode, self.cfg.flags | L.FLAG_COUNT, self.cfg.batch)
         for q in self.parts:
             q["status"][L.ST_PAIRS] = 0
             q["status"][L.ST_CANDIDATES] = 0
@@ -222,9 +223,10 @@ def default_cache_path():
 
 
 def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persistent=(False, True),
-             reps=10, cache_path=None, use_cache=True, tight=False):
-    """Times every (tile shape, persistent) candidate with graph replays and
-    returns {"tile": (w, h), "persistent": bool, "ms": t, "timings": [...]}."""
+             reps=10, cache_path=None, use_cache=True, tight=False, batches=(256, 128)):
+    """Times every (tile shape, persistent launch, staging batch) candidate with
+    graph replays and returns {"tile": (w, h), "persistent": bool, "batch": b,
+    "ms": t, "timings": [...]}."""
     cache_path = cache_path or default_cache_path()
     key = _bucket_key(g["means"].shape[0], cams, mode, backward, tight)
     cache = {}
@@ -235,36 +237,39 @@ def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persis
             cache = {}
         if key in cache:
             c = cache[key]
-            return {"tile": tuple(c["tile"]), "persistent": c["persistent"], "ms": c["ms"],
-                    "timings": c.get("timings", []), "cached": True}
+            return {"tile": tuple(c["tile"]), "persistent": c["persistent"], "batch": c.get("batch", 256),
+                    "ms": c["ms"], "timings": c.get("timings", []), "cached": True}
     timings = []
     for tile in shapes:
         for pers in persistent:
             if pers and mode != "localgs":
                 continue
-            r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward, tight=tight)
-            if backward:
-                r.d_rgb.fill_(1.0 / r.d_rgb.numel())
-            r.capture()
-            ts = []
-            for _ in range(reps + 2):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                r.graph.replay()
-                e1.record()
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            r.check()
-            timings.append({"tile": list(tile), "persistent": pers, "ms": float(np.median(ts[2:]))})
-            del r
-            torch.cuda.empty_cache()
+            for nb in (batches if mode == "localgs" else (256,)):
+                r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward, tight=tight,
+                             batch=nb)
+                if backward:
+                    r.d_rgb.fill_(1.0 / r.d_rgb.numel())
+                r.capture()
+                ts = []
+                for _ in range(reps + 2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    r.graph.replay()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                r.check()
+                timings.append({"tile": list(tile), "persistent": pers, "batch": nb,
+                                "ms": float(np.median(ts[2:]))})
+                del r
+                torch.cuda.empty_cache()
     best = min(timings, key=lambda t: t["ms"])
-    cache[key] = {"tile": best["tile"], "persistent": best["persistent"], "ms": best["ms"],
-                  "timings": timings}
+    cache[key] = {"tile": best["tile"], "persistent": best["persistent"], "batch": best["batch"],
+                  "ms": best["ms"], "timings": timings}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1)
     except OSError:
         pass
-    return {"tile": tuple(best["tile"]), "persistent": best["persistent"], "ms": best["ms"],
-            "timings": timings, "cached": False}
+    return {"tile": tuple(best["tile"]), "persistent": best["persistent"], "batch": best["batch"],
+            "ms": best["ms"], "timings": timings, "cached": False}

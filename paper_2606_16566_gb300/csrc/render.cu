@@ -132,9 +132,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //                precision study.
 constexpr int VAR_CONTRACT = 0, VAR_LITERAL = 1, VAR_GLOBAL = 2;
 
-template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT>
+template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT, int NB = BATCH>
 __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t tile,
                                              LocalSmem& S) {
+    static_assert(NB == 64 || NB == 128 || NB == 256, "staging batch of 64, 128 or 256 Gaussians");
     float4* sV = S.sV;
     float2* sDE = S.sDE;
     float4* sC = S.sC;
@@ -159,14 +160,14 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     bool warp_done = __all_sync(0xffffffffu, done);
     uint32_t pairs = 0, cands = 0;
 
-    // Staging: thread i copies the three 16-B records of list entry b0 + i with
-    // cp.async into buffer (b0 / BATCH) & 1, one batch ahead, so the gathers of
-    // batch b+1 are in flight while batch b blends. A thread reads back only
+    // Staging: thread i < NB copies the three 16-B records of list entry b0 + i
+    // with cp.async into buffer (b0 / NB) & 1, one batch ahead, so the gathers
+    // of batch b+1 are in flight while batch b blends. A thread reads back only
     // the slots it copied itself, so its own group fence orders them.
     const int ti = threadIdx.x;
     auto stage = [&](uint32_t b, int buf) {
         const uint32_t jj = b + (uint32_t)ti;
-        if (jj < t.count) {
+        if (ti < NB && jj < t.count) {
             const uint32_t id = p.vals[t.start + jj];
             cp_async16(&S.raw[buf][0][ti], p.xy + id);
             cp_async16(&S.raw[buf][1][ti], p.conic + id);
@@ -176,13 +177,13 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     };
     if (t.count > 0 && !__syncthreads_and(warp_done)) stage(0, 0);
     int buf = 0;
-    for (uint32_t b0 = 0; b0 < t.count; b0 += BATCH, buf ^= 1) {
+    for (uint32_t b0 = 0; b0 < t.count; b0 += NB, buf ^= 1) {
         if (__syncthreads_and(warp_done)) break;
-        if (b0 + BATCH < t.count) stage(b0 + BATCH, buf ^ 1);
+        if (b0 + NB < t.count) stage(b0 + NB, buf ^ 1);
         else cp_async_commit();
         cp_async_wait<1>();
         const uint32_t j = b0 + threadIdx.x;
-        if (j < t.count) {
+        if (ti < NB && j < t.count) {
             const float4 xy = S.raw[buf][0][ti];
             const float4 co = S.raw[buf][1][ti];
             const float4 col = S.raw[buf][2][ti];
@@ -199,7 +200,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                                                          __fadd_rn(xy.y, xy.w), t.X0, t.Y0);
         }
         __syncthreads();
-        const int nb = (int)min((uint32_t)BATCH, t.count - b0);
+        const int nb = (int)min((uint32_t)NB, t.count - b0);
         if (COUNT && !warp_done) cands += (uint32_t)nb;
         if (!warp_done) {
             // compact the warp's list: the batch indices whose mask bit for this
@@ -274,16 +275,16 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
 }
 
 // One CTA per tile.
-template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT>
+template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT, int NB = BATCH>
 __global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
     __shared__ LocalSmem S;
-    localgs_tile<TW, TH, COUNT, VAR>(p, vs, blockIdx.x, S);
+    localgs_tile<TW, TH, COUNT, VAR, NB>(p, vs, blockIdx.x, S);
 }
 
 // Persistent CTAs: each pulls the next tile index from a work-queue counter
 // (status word LGS_ST_QUEUE, zeroed by the launcher) until all tiles are taken,
 // so uneven tile lists and uneven view sizes balance across the SMs.
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, int NB = BATCH>
 __global__ void __launch_bounds__(256) render_localgs_persistent(RenderParams p, Views vs) {
     __shared__ LocalSmem S;
     __shared__ uint32_t s_tile;
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(256) render_localgs_persistent(RenderParams p,
         const uint32_t tile = s_tile;
         __syncthreads();
         if (tile >= vs.n_tiles) break;
-        localgs_tile<TW, TH, COUNT>(p, vs, tile, S);
+        localgs_tile<TW, TH, COUNT, VAR_CONTRACT, NB>(p, vs, tile, S);
         __syncthreads();
     }
 }
@@ -351,37 +352,52 @@ __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
                   (unsigned long long)pairs * 32ull);
 }
 
+// The Local-GS contract kernel for one staging batch size (one CTA per tile or
+// persistent CTAs pulling tiles from the work queue).
+template <int TW, int TH, int NB>
+lgs_status launch_contract(const RenderParams& p, const Views& vs, bool count, bool persistent,
+                           cudaStream_t s) {
+    const dim3 grid(vs.n_tiles), block(256);
+    if (!persistent) {
+        if (count) render_localgs<TW, TH, true, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
+        else       render_localgs<TW, TH, false, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
+        return cuda_status(cudaGetLastError());
+    }
+    if (cudaMemsetAsync(p.status + LGS_ST_QUEUE, 0, sizeof(int64_t), s) != cudaSuccess) return LGS_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (count) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, true, NB>, 256, 0);
+        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+        render_localgs_persistent<TW, TH, true, NB><<<g, block, 0, s>>>(p, vs);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, false, NB>, 256, 0);
+        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+        render_localgs_persistent<TW, TH, false, NB><<<g, block, 0, s>>>(p, vs);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
 template <int TW, int TH>
-lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, bool count,
+lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, int batch, bool count,
                          bool persistent, cudaStream_t s) {
     const dim3 grid(vs.n_tiles), block(256);
     if (mode == LGS_MODE_PLAIN) {
         if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_plain<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
-    } else if (persistent && mode == LGS_MODE_LOCALGS) {
-        if (cudaMemsetAsync(p.status + LGS_ST_QUEUE, 0, sizeof(int64_t), s) != cudaSuccess)
-            return LGS_ERR_CUDA;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (count) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, true>, 256, 0);
-            const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
-            render_localgs_persistent<TW, TH, true><<<g, block, 0, s>>>(p, vs);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, false>, 256, 0);
-            const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
-            render_localgs_persistent<TW, TH, false><<<g, block, 0, s>>>(p, vs);
-        }
     } else if (mode == LGS_MODE_LITERAL) {
         if (count) render_localgs<TW, TH, true, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
         else       render_localgs<TW, TH, false, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
     } else if (mode == LGS_MODE_GLOBAL) {
         if (count) render_localgs<TW, TH, true, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
         else       render_localgs<TW, TH, false, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
+    } else if (batch == 64) {
+        return launch_contract<TW, TH, 64>(p, vs, count, persistent, s);
+    } else if (batch == 128) {
+        return launch_contract<TW, TH, 128>(p, vs, count, persistent, s);
     } else {
-        if (count) render_localgs<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
-        else       render_localgs<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
+        return launch_contract<TW, TH, 256>(p, vs, count, persistent, s);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -403,6 +419,8 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     if (st != LGS_OK) return st;
     if (cfg->mode < LGS_MODE_LOCALGS || cfg->mode > LGS_MODE_GLOBAL) return LGS_ERR_UNSUPPORTED;
     if ((cfg->flags & LGS_FLAG_PERSISTENT) && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
+    if (cfg->batch != 0 && cfg->batch != 64 && cfg->batch != 128 && cfg->batch != 256) return LGS_ERR_UNSUPPORTED;
+    const int batch = cfg->batch == 0 ? BATCH : cfg->batch;
     if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
     RenderParams p;
     p.xy = reinterpret_cast<const float4*>(pre->xy);
@@ -417,7 +435,7 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     const bool count = (cfg->flags & LGS_FLAG_COUNT) != 0;
     const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, count, persistent, s);
-    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, count, persistent, s);
-    return launch_render<32, 8>(p, vs, cfg->mode, count, persistent, s);
+    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, batch, count, persistent, s);
+    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, batch, count, persistent, s);
+    return launch_render<32, 8>(p, vs, cfg->mode, batch, count, persistent, s);
 }

@@ -4,6 +4,7 @@ import pytest
 import torch
 
 from paper_2606_16566_gb300 import batch, lgs, scenes
+from paper_2606_16566_gb300 import _lib as L
 
 from parity import assert_image_parity, full_view_parity, to_numpy_view
 
@@ -69,7 +70,8 @@ def test_autotune_picks_a_measured_candidate(tmp_path):
     g = lgs.to_device(sc)
     res = batch.autotune(g, cams, reps=3, cache_path=str(tmp_path / "tune.json"))
     assert tuple(res["tile"]) in batch.TILE_SHAPES
-    assert len(res["timings"]) == 6
+    assert len(res["timings"]) == 12
+    assert res["batch"] in (128, 256)
     assert res["ms"] == min(t["ms"] for t in res["timings"])
     again = batch.autotune(g, cams, reps=3, cache_path=str(tmp_path / "tune.json"))
     assert again["cached"] and tuple(again["tile"]) == tuple(res["tile"])
@@ -136,3 +138,30 @@ def test_view_groups_change_no_output():
     for k in ("means", "scales", "quats", "opacities", "sh"):
         d = (one.grads[k] - many.grads[k]).norm() / one.grads[k].norm().clamp_min(1e-30)
         assert d.item() <= 1e-4, k
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_staging_batch_sizes_change_no_output(persistent):
+    """Staging 64, 128 or 256 Gaussians per round gives bit-identical outputs."""
+    sc, _ = scenes.outdoor(n=40000)
+    cams = _uneven_views(4, seed=8)
+    g = lgs.to_device(sc)
+    outs = []
+    for nb in (256, 128, 64):
+        r = batch.Renderer(g, cams, tight=True, persistent=persistent, batch=nb)
+        r.forward()
+        torch.cuda.synchronize()
+        r.check()
+        outs.append((r.rgb.clone(), r.T.clone(), r.nc.clone()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
+def test_unsupported_staging_batch_is_rejected():
+    sc, cams = scenes.random_small(200, seed=9)
+    g = lgs.to_device(sc)
+    res = lgs.render(g, cams)
+    with pytest.raises(L.LgsError) as e:
+        lgs.render_fwd(res["pre"], res["vals"], res["ranges"], cams, lgs.config(batch=96))
+    assert e.value.code == L.LGS_ERR_UNSUPPORTED
