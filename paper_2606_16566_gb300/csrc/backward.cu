@@ -16,11 +16,15 @@
 //   dL/dalpha_k = T_k <rgb_k - A_k, g> - T_f (<bg, g> + gT) / (1 - alpha_k)
 // with A_k the colour behind k normalised by T_{k+1} (A <- alpha rgb + (1-alpha) A).
 // Since ln(alpha) = V . B_local (hoist transform), dL/dV = (dL/dalpha alpha) B_local:
-// six hoisted gradients plus three colour gradients per pair, summed over the
-// warp's 32 pixels with a transposed shuffle reduction (9 values in 14
-// shuffles), over the CTA's 8 warps with shared-memory atomics, and mapped
-// once per (Gaussian, tile) through the transpose of the hoist Jacobian to
-// dL/d(a, b, c, o, u, v) before one global atomic per component.
+// six hoisted gradients plus three colour gradients per pair. The sums over
+// the warp's 32 pixels are deferred: each lane leaves dp = dL/dalpha alpha and
+// w = alpha T of its pixel in a row of a per-warp buffer, and every 8 rows the
+// lanes reduce the buffer with one Gaussian per lane group and one pixel row
+// per lane (the monomials of B_local are constants of the lane's row), so a
+// pair costs two shared stores instead of a 9-value shuffle reduction. The
+// per-warp sums meet over the CTA's 8 warps in shared-memory atomics and are
+// mapped once per (Gaussian, tile) through the transpose of the hoist Jacobian
+// to dL/d(a, b, c, o, u, v) before one global atomic per component.
 //
 // preprocess_bwd: one thread per Gaussian looping over the views, chain rule
 // through conic inversion (dL/dSigma' = -Q dL/dQ Q), Sigma' = M M^T + 0.3 I with
@@ -91,6 +95,67 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// Per-warp buffer of the deferred reduction: up to RED_ROWS rows, one per
+// Gaussian of the warp's list, each holding the 32 lanes' dp and w. The 16-B
+// column group c of row r is stored at group c ^ r, so that the row writes of
+// the walk (32 lanes, one row) and the 16-B reads of the reduction (8 rows, one
+// column group) both hit distinct banks.
+constexpr int RED_ROWS = 8;
+struct BwdRed {
+    float dp[RED_ROWS][32];
+    float w[RED_ROWS][32];
+    uint32_t slot[RED_ROWS];   // batch index of the row's Gaussian
+};
+
+__device__ __forceinline__ int red_col(int row, int col) {
+    return ((((col >> 2) ^ row) & 7) << 2) | (col & 3);
+}
+
+// Reduces rows 0..ns-1 of the warp's buffer into sG. Lane (e, q) = (lane & 7,
+// lane >> 3) sums row e over the strip pixels q*8 .. q*8+7, which lie in one
+// pixel row (the tile width is a multiple of 8) at columns centred on xc with
+// local y coordinate yq: with offsets u = ii - 3.5 the moments of the group are
+// S0 = sum dp, Sx = xc S0 + sum dp u, Sxx = xc^2 S0 + 2 xc sum dp u + sum dp u^2,
+// and sum dp x y = yq Sx, sum dp y^2 = yq^2 S0, sum dp y = yq S0. Two shuffle
+// levels add the four row groups; lanes 0..ns-1 then hold the warp's sums.
+__device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float4* gp, float xc, float yq,
+                                            float (*sG)[9], int lane) {
+    const int e = lane & 7, q = lane >> 3;
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f, W0 = 0.f, W1 = 0.f, W2 = 0.f;
+    if (e < ns) {
+        const float4 d0 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, 8 * q)]);
+        const float4 d1 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, 8 * q + 4)]);
+        const float4 w0 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, 8 * q)]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, 8 * q + 4)]);
+        const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+            const float u = (float)ii - 3.5f;
+            S0 += d[ii];
+            S1 = fmaf(d[ii], u, S1);
+            S2 = fmaf(d[ii], u * u, S2);
+            const float4 g = gp[8 * q + ii];
+            W0 = fmaf(ww[ii], g.x, W0);
+            W1 = fmaf(ww[ii], g.y, W1);
+            W2 = fmaf(ww[ii], g.z, W2);
+        }
+    }
+    const float Sx = fmaf(xc, S0, S1);
+    const float Sxx = fmaf(xc, fmaf(xc, S0, 2.f * S1), S2);
+    float v[9] = {Sxx, yq * Sx, yq * yq * S0, Sx, yq * S0, W0, W1, S0, W2};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 8);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
+    }
+    if (q == 0 && e < ns) {
+        float* dst = sG[R.slot[e]];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) atomicAdd(dst + k, v[k]);
+    }
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views vs) {
     __shared__ float4 sV[BWD_BATCH];
@@ -101,6 +166,9 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
     __shared__ uint32_t sId[BWD_BATCH];
     __shared__ float sG[BWD_BATCH][9];
     __shared__ uint32_t sLast[8];
+    __shared__ __align__(16) BwdRed sR[8];
+    __shared__ float4 sGp[256];   // (dL/drgb of the thread's pixel, 0)
+    static_assert(TW % 8 == 0, "row groups of 8 pixels");
 
     const uint32_t tile = blockIdx.x;
     const int view = view_of_tile(vs, tile);
@@ -109,6 +177,10 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
     const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = lane % TW, ly = warp * (TH / 8) + lane / TW;
+    // the pixel row group this lane reduces (see reduce_rows)
+    const int gq = 8 * (lane >> 3);
+    const float xc = (float)(gq % TW) + 3.5f - 0.5f * (TW - 1);
+    const float yq = (float)(warp * (TH / 8) + gq / TW) - 0.5f * (TH - 1);
     const int px = X0 + lx, py = Y0 + ly;
     const bool inside = px < c.W && py < c.H;
     const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
@@ -132,6 +204,8 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
         const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
         tail = T * (c.bg[0] * g0 + c.bg[1] * g1 + c.bg[2] * g2 + gT);
     }
+    sGp[threadIdx.x] = make_float4(g0, g1, g2, 0.f);
+    BwdRed& R = sR[warp];
     float A0 = 0.f, A1 = 0.f, A2 = 0.f;
     uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
     if (lane == 0) sLast[warp] = wlast;
@@ -180,48 +254,48 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
                 nl += __popc(bal);
             }
             __syncwarp();
-            {
+            int ns = 0;   // rows of the warp's buffer in use
 #pragma unroll 4
-                for (int i = nl - 1; i >= 0; --i) {
-                    const int g = sLw[i];
-                    const float4 V = sV[g];
-                    const float2 DE = sDE[g];
-                    const float4 col = sC[g];
-                    const uint32_t pos = __float_as_uint(col.w);
-                    const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
-                                     fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
-                    const bool contrib = pos <= last && pw >= LOG2_ALPHA_MIN_B;
-                    if (!__any_sync(0xffffffffu, contrib)) continue;   // nothing to reduce
-                    const float e2 = ex2_approx_b(pw);
-                    const float al = fminf(0.99f, e2);
-                    // branch-free: lanes that do not contribute get alpha 0, which
-                    // leaves T and the accumulated colour exactly as they were
-                    float v[8];
-                    const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
-                    const float Tk = T * inv;
-                    const float ac = contrib ? al : 0.f;
-                    const float w = ac * Tk;
-                    v[5] = w * g0;
-                    v[6] = w * g1;
-                    const float gb = w * g2;
-                    const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
-                    const float dal = Tk * cg - tail * inv;
-                    A0 = fmaf(ac, col.x - A0, A0);
-                    A1 = fmaf(ac, col.y - A1, A1);
-                    A2 = fmaf(ac, col.z - A2, A2);
-                    T = contrib ? Tk : T;
-                    const float dp = (contrib && !(e2 > 0.99f)) ? dal * al : 0.f;
-                    v[0] = dp * bx2;
-                    v[1] = dp * bxy;
-                    v[2] = dp * by2;
-                    v[3] = dp * xl;
-                    v[4] = dp * yl;
-                    v[7] = dp;
-                    const float s8 = warp_sum8_transposed(v);
-                    const float s9 = warp_sum(gb);
-                    if ((lane & 3) == 0) atomicAdd(&sG[g][lane >> 2], s8);
-                    if (lane == 0) atomicAdd(&sG[g][8], s9);
+            for (int i = nl - 1; i >= 0; --i) {
+                const int g = sLw[i];
+                const float4 V = sV[g];
+                const float2 DE = sDE[g];
+                const float4 col = sC[g];
+                const uint32_t pos = __float_as_uint(col.w);
+                const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
+                                 fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
+                const bool contrib = pos <= last && pw >= LOG2_ALPHA_MIN_B;
+                if (!__any_sync(0xffffffffu, contrib)) continue;   // nothing to reduce
+                const float e2 = ex2_approx_b(pw);
+                const float al = fminf(0.99f, e2);
+                // branch-free: lanes that do not contribute get alpha 0, which
+                // leaves T and the accumulated colour exactly as they were
+                const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
+                const float Tk = T * inv;
+                const float ac = contrib ? al : 0.f;
+                const float w = ac * Tk;
+                const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
+                const float dal = Tk * cg - tail * inv;
+                A0 = fmaf(ac, col.x - A0, A0);
+                A1 = fmaf(ac, col.y - A1, A1);
+                A2 = fmaf(ac, col.z - A2, A2);
+                T = contrib ? Tk : T;
+                const float dp = (contrib && !(e2 > 0.99f)) ? dal * al : 0.f;
+                const int cc = red_col(ns, lane);
+                R.dp[ns][cc] = dp;
+                R.w[ns][cc] = w;
+                if (lane == 0) R.slot[ns] = (uint32_t)g;
+                if (++ns == RED_ROWS) {
+                    __syncwarp();
+                    reduce_rows(R, ns, sGp + 32 * warp, xc, yq, sG, lane);
+                    __syncwarp();
+                    ns = 0;
                 }
+            }
+            if (ns > 0) {
+                __syncwarp();
+                reduce_rows(R, ns, sGp + 32 * warp, xc, yq, sG, lane);
+                __syncwarp();
             }
         }
         __syncthreads();
