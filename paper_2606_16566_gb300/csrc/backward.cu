@@ -97,9 +97,9 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 // Per-warp buffer of the deferred reduction: up to RED_ROWS rows, one per
 // Gaussian of the warp's list, each holding the 32 lanes' dp and w. The 16-B
-// column group c of row r is stored at group c ^ r, so that the row writes of
-// the walk (32 lanes, one row) and the 16-B reads of the reduction (8 rows, one
-// column group) both hit distinct banks.
+// column group c of row r is stored at group c ^ (r & 7), so that the row
+// writes of the walk (32 lanes, one row) and the 16-B reads of the reduction
+// (8 rows, one column group each) both hit distinct banks.
 constexpr int RED_ROWS = 8;
 struct BwdRed {
     float dp[RED_ROWS][32];
@@ -111,43 +111,57 @@ __device__ __forceinline__ int red_col(int row, int col) {
     return ((((col >> 2) ^ row) & 7) << 2) | (col & 3);
 }
 
-// Reduces rows 0..ns-1 of the warp's buffer into sG. Lane (e, q) = (lane & 7,
-// lane >> 3) sums row e over the strip pixels q*8 .. q*8+7, which lie in one
-// pixel row (the tile width is a multiple of 8) at columns centred on xc with
-// local y coordinate yq: with offsets u = ii - 3.5 the moments of the group are
-// S0 = sum dp, Sx = xc S0 + sum dp u, Sxx = xc^2 S0 + 2 xc sum dp u + sum dp u^2,
-// and sum dp x y = yq Sx, sum dp y^2 = yq^2 S0, sum dp y = yq S0. Two shuffle
-// levels add the four row groups; lanes 0..ns-1 then hold the warp's sums.
-__device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float4* gp, float xc, float yq,
-                                            float (*sG)[9], int lane) {
-    const int e = lane & 7, q = lane >> 3;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f, W0 = 0.f, W1 = 0.f, W2 = 0.f;
+// Reduces rows 0..ns-1 of the warp's buffer into sG. Lane (e, q) = (lane %
+// RED_ROWS, lane / RED_ROWS) sums row e over the RED_ROWS strip pixels starting
+// at q * RED_ROWS, in groups of 8 that each lie in one pixel row (the tile width
+// is a multiple of 8). A group centred on column xc of local row y has, with
+// offsets u = ii - 3.5, S0 = sum dp, Sx = xc S0 + sum dp u and
+// Sxx = xc^2 S0 + 2 xc sum dp u + sum dp u^2, and sum dp x y = y Sx,
+// sum dp y^2 = y^2 S0, sum dp y = y S0. Shuffles add the lanes of a row; lanes
+// 0..ns-1 then hold the warp's sums.
+template <int TW, int TH>
+__device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float4* gp, float (*sG)[9],
+                                            int lane, int warp) {
+    constexpr int PIX = RED_ROWS;   // pixels per lane
+    const int e = lane % RED_ROWS, q = lane / RED_ROWS;
+    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (e < ns) {
-        const float4 d0 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, 8 * q)]);
-        const float4 d1 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, 8 * q + 4)]);
-        const float4 w0 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, 8 * q)]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, 8 * q + 4)]);
-        const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-        const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) {
-            const float u = (float)ii - 3.5f;
-            S0 += d[ii];
-            S1 = fmaf(d[ii], u, S1);
-            S2 = fmaf(d[ii], u * u, S2);
-            const float4 g = gp[8 * q + ii];
-            W0 = fmaf(ww[ii], g.x, W0);
-            W1 = fmaf(ww[ii], g.y, W1);
-            W2 = fmaf(ww[ii], g.z, W2);
+        for (int sg = 0; sg < PIX / 8; ++sg) {
+            const int pb = q * PIX + 8 * sg;                 // first pixel of the group
+            const float xc = (float)(pb % TW) + 3.5f - 0.5f * (TW - 1);
+            const float y = (float)(warp * (TH / 8) + pb / TW) - 0.5f * (TH - 1);
+            const float4 d0 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, pb)]);
+            const float4 d1 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, pb + 4)]);
+            const float4 w0 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, pb)]);
+            const float4 w1 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, pb + 4)]);
+            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < 8; ++ii) {
+                const float u = (float)ii - 3.5f;
+                S0 += d[ii];
+                S1 = fmaf(d[ii], u, S1);
+                S2 = fmaf(d[ii], u * u, S2);
+                const float4 g = gp[pb + ii];
+                v[5] = fmaf(ww[ii], g.x, v[5]);
+                v[6] = fmaf(ww[ii], g.y, v[6]);
+                v[8] = fmaf(ww[ii], g.z, v[8]);
+            }
+            const float Sx = fmaf(xc, S0, S1);
+            v[0] += fmaf(xc, fmaf(xc, S0, 2.f * S1), S2);
+            v[1] = fmaf(y, Sx, v[1]);
+            v[2] = fmaf(y * y, S0, v[2]);
+            v[3] += Sx;
+            v[4] = fmaf(y, S0, v[4]);
+            v[7] += S0;
         }
     }
-    const float Sx = fmaf(xc, S0, S1);
-    const float Sxx = fmaf(xc, fmaf(xc, S0, 2.f * S1), S2);
-    float v[9] = {Sxx, yq * Sx, yq * yq * S0, Sx, yq * S0, W0, W1, S0, W2};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 8);
-        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
+#pragma unroll
+        for (int o = RED_ROWS; o < 32; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
     if (q == 0 && e < ns) {
         float* dst = sG[R.slot[e]];
@@ -177,10 +191,6 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
     const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = lane % TW, ly = warp * (TH / 8) + lane / TW;
-    // the pixel row group this lane reduces (see reduce_rows)
-    const int gq = 8 * (lane >> 3);
-    const float xc = (float)(gq % TW) + 3.5f - 0.5f * (TW - 1);
-    const float yq = (float)(warp * (TH / 8) + gq / TW) - 0.5f * (TH - 1);
     const int px = X0 + lx, py = Y0 + ly;
     const bool inside = px < c.W && py < c.H;
     const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
     }
     sGp[threadIdx.x] = make_float4(g0, g1, g2, 0.f);
     BwdRed& R = sR[warp];
-    float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+    float Ag = 0.f;   // <A, g>: the colour behind the current Gaussian, projected on g
     uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
     if (lane == 0) sLast[warp] = wlast;
     __syncthreads();
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
             }
             __syncwarp();
             int ns = 0;   // rows of the warp's buffer in use
-#pragma unroll 4
+#pragma unroll 1
             for (int i = nl - 1; i >= 0; --i) {
                 const int g = sLw[i];
                 const float4 V = sV[g];
@@ -274,11 +284,10 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
                 const float Tk = T * inv;
                 const float ac = contrib ? al : 0.f;
                 const float w = ac * Tk;
-                const float cg = (col.x - A0) * g0 + (col.y - A1) * g1 + (col.z - A2) * g2;
+                // <rgb_k - A_k, g>, and A <- alpha rgb + (1 - alpha) A carried as <A, g>
+                const float cg = fmaf(col.z, g2, fmaf(col.y, g1, col.x * g0)) - Ag;
                 const float dal = Tk * cg - tail * inv;
-                A0 = fmaf(ac, col.x - A0, A0);
-                A1 = fmaf(ac, col.y - A1, A1);
-                A2 = fmaf(ac, col.z - A2, A2);
+                Ag = fmaf(ac, cg, Ag);
                 T = contrib ? Tk : T;
                 const float dp = (contrib && !(e2 > 0.99f)) ? dal * al : 0.f;
                 const int cc = red_col(ns, lane);
@@ -287,14 +296,14 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
                 if (lane == 0) R.slot[ns] = (uint32_t)g;
                 if (++ns == RED_ROWS) {
                     __syncwarp();
-                    reduce_rows(R, ns, sGp + 32 * warp, xc, yq, sG, lane);
+                    reduce_rows<TW, TH>(R, ns, sGp + 32 * warp, sG, lane, warp);
                     __syncwarp();
                     ns = 0;
                 }
             }
             if (ns > 0) {
                 __syncwarp();
-                reduce_rows(R, ns, sGp + 32 * warp, xc, yq, sG, lane);
+                reduce_rows<TW, TH>(R, ns, sGp + 32 * warp, sG, lane, warp);
                 __syncwarp();
             }
         }
