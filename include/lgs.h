@@ -278,7 +278,7 @@ lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams, int32_
  * the caller's workspace of LGS_SELFTEST_WORKSPACE_BYTES (device, 256-B
  * aligned). Afterwards d_status holds LGS_ERR_TIMEOUT with detail 1. Nothing
  * faults or traps; the context stays usable. */
-#define LGS_SELFTEST_WORKSPACE_BYTES (160ull << 10)
+#define LGS_SELFTEST_WORKSPACE_BYTES (256ull << 10)
 lgs_status lgs_selftest_wait_timeout(int32_t spin_limit, void* workspace, size_t workspace_bytes,
                                      int64_t* d_status, void* stream);
 

@@ -24,7 +24,7 @@ LGS_ERR_INTERNAL = 8
 LGS_MAX_VIEWS = 64
 SORT_STATIC_MAX_ENTRIES = 1 << 18
 SORT_STATIC_MAX_INSTANCES = 1 << 20
-SELFTEST_WORKSPACE_BYTES = 160 << 10
+SELFTEST_WORKSPACE_BYTES = 256 << 10
 LGS_STATUS_WORDS = 8
 ST_CODE, ST_DETAIL, ST_NUM_INSTANCES, ST_NONFINITE, ST_PAIRS, ST_QUEUE, ST_QUEUE_BWD, ST_CANDIDATES = range(8)
 

@@ -22,7 +22,7 @@
 // entry index), so the result is bit for bit the stable sort of the 64-bit
 // keys -- with 4 passes over the (visible) entries instead of 4 passes over the K
 // instances for the depth bits.
-// Every radix pass is one "onesweep" kernel: per 4096-element block a stable
+// Every radix pass is one "onesweep" kernel: per 6144-element block a stable
 // in-shared-memory ranking and a decoupled look-back over the earlier blocks'
 // digit counts (see onesweep_pass).
 #include "common.cuh"
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
 // ------------------------------------------------------------------ radix passes (onesweep)
 // A stable LSD pass moves (u32 key, u32 value) pairs by one 8-bit digit in a
 // single kernel. Each block takes the next tile index in launch order
-// (atomic counter), counts its 4096 keys' digits in shared memory and
+// (atomic counter), counts its 6144 keys' digits in shared memory and
 // publishes those counts at once, obtains the count of every digit in all
 // earlier tiles by looking back over their published words (decoupled
 // look-back, Merrill & Garland): a word carries either the tile's own count
@@ -436,8 +436,8 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
 // entries (no tile) altogether, so later passes and stages see only the
 // visible entries; their number goes to a device word.
 constexpr int OS_THREADS = 256;
-constexpr int OS_ITEMS = 16;
-constexpr int OS_TILE = OS_THREADS * OS_ITEMS;   // 4096
+constexpr int OS_ITEMS = 24;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;   // 6144
 constexpr uint64_t OS_AGG = 1ull << 62;
 constexpr uint64_t OS_PRE = 2ull << 62;
 constexpr uint64_t OS_VAL = (1ull << 62) - 1;
@@ -577,17 +577,17 @@ struct OneSmem {
     uint32_t vals[OS_TILE];
 };
 
-// Keys are ranked warp by warp: warp w owns tile elements [w*512, (w+1)*512),
+// Keys are ranked warp by warp: warp w owns tile elements [w*768, (w+1)*768),
 // taken 32 at a time in order; per-bit ballots group equal digits and the
 // warp's private counters give each key its rank among equal digits of the
 // warp's range, with no block barrier. A digit-major exclusive scan over
 // (digit, warp) then gives each (digit, warp) pair its place in the tile.
-__global__ void __launch_bounds__(OS_THREADS, 3) onesweep_pass(
+__global__ void __launch_bounds__(OS_THREADS, 2) onesweep_pass(
     OsSrc src, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* cnt,
     int64_t count, int shift, const uint32_t* bases, unsigned long long* look, uint32_t* tile_counter,
     int64_t* err_status, int spin_limit) {
     constexpr int NW = OS_THREADS / 32;
-    constexpr int PER_WARP = OS_TILE / NW;      // 512
+    constexpr int PER_WARP = OS_TILE / NW;      // 768
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OneSmem& S = *reinterpret_cast<OneSmem*>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
