@@ -238,7 +238,7 @@ lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, i
  * caller. */
 #define LGS_SORT_STATIC_MAX_ENTRIES (1ll << 18)
 #define LGS_SORT_STATIC_MAX_INSTANCES (1ll << 20)
-#define LGS_SORT_STATIC_BYTES (20ull << 20)
+#define LGS_SORT_STATIC_BYTES (28ull << 20)
 lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams,
                            int32_t n_views, const lgs_config* cfg, int64_t capacity,
                            uint64_t* keys, uint32_t* vals, uint32_t* ranges, int64_t* d_status,

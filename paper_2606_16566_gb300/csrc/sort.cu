@@ -246,9 +246,12 @@ struct TightLane {
     TightBox tb;
 };
 
+// Loads a visible entry's rect, conic and mean and forms its tight box; with
+// `rec`, also writes the entry's emission record at depth-order index idx.
 __device__ __forceinline__ TightLane tight_lane_load(uint32_t ent, bool live, const uint64_t* rect,
                                                      const float4* xy, const float4* conic,
-                                                     const Views& vs, int64_t n) {
+                                                     const Views& vs, int64_t n, uint4* rec = nullptr,
+                                                     int64_t idx = 0) {
     TightLane L{};
     L.gx = 1;
     L.ent = ent;
@@ -263,7 +266,37 @@ __device__ __forceinline__ TightLane tight_lane_load(uint32_t ent, bool live, co
         L.gx = (uint32_t)cv.gx;
         const float4 co = conic[ent];
         const float4 p = xy[ent];
-        L.tb = tight_box(co.x, co.y, co.z, co.w, __fadd_rn(p.x, p.z), __fadd_rn(p.y, p.w));
+        const float mux = __fadd_rn(p.x, p.z), muy = __fadd_rn(p.y, p.w);
+        L.tb = tight_box(co.x, co.y, co.z, co.w, mux, muy);
+        if (rec) {
+            rec[2 * idx] = make_uint4((uint32_t)r, (uint32_t)(r >> 32), __float_as_uint(mux), __float_as_uint(muy));
+            rec[2 * idx + 1] = make_uint4(__float_as_uint(co.x), __float_as_uint(co.y), __float_as_uint(co.z),
+                                          __float_as_uint(co.w));
+        }
+    }
+    return L;
+}
+
+// The same lane state from the emission record count_tight left at depth-order
+// index idx ((rect, mean x, mean y), conic: two coalesced 16-B loads instead of
+// a second gather of rect, conic and mean).
+__device__ __forceinline__ TightLane tight_lane_rec(uint32_t ent, bool live, const uint4* rec, int64_t idx,
+                                                    const Views& vs, int64_t n) {
+    TightLane L{};
+    L.gx = 1;
+    L.ent = ent;
+    if (live) {
+        const uint4 a = rec[2 * idx];
+        const uint4 c = rec[2 * idx + 1];
+        L.x0 = a.x & 0xffffu;
+        L.y0 = a.x >> 16;
+        L.wd = (a.y & 0xffffu) - L.x0;
+        L.y1 = a.y >> 16;
+        const ViewRec& cv = vs.v[(int)(ent / (uint64_t)n)];
+        L.toff = cv.tile_off;
+        L.gx = (uint32_t)cv.gx;
+        L.tb = tight_box(__uint_as_float(c.x), __uint_as_float(c.y), __uint_as_float(c.z), __uint_as_float(c.w),
+                         __uint_as_float(a.z), __uint_as_float(a.w));
     }
     return L;
 }
@@ -313,7 +346,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
                                                    const uint64_t* rect, const float4* xy,
                                                    const float4* conic, int64_t m, const int64_t* mv,
-                                                   int64_t n, Views vs, uint32_t* tiles_sorted) {
+                                                   int64_t n, Views vs, uint32_t* tiles_sorted, uint4* rec) {
     __shared__ uint32_t cnt[256];
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
@@ -325,7 +358,7 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
     const uint32_t ent = visible ? order[idx] : 0u;
     // the first entry pass kept only visible entries, so every entry before
     // the visible count has a non-empty rect
-    const TightLane L = tight_lane_load(ent, visible, rect, xy, conic, vs, n);
+    const TightLane L = tight_lane_load(ent, visible, rect, xy, conic, vs, n, rec, idx);
     cnt[threadIdx.x] = 0u;
     __syncwarp();
     const uint32_t iw = warp_inclusive_sum(L.wd);
@@ -357,8 +390,7 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
 // with tile 0 / entry 0 and records LGS_ERR_INTERNAL.
 template <int TW, int TH>
 __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, const uint32_t* tiles_sorted,
-                                                        const uint32_t* offsets, const uint64_t* rect,
-                                                        const float4* xy, const float4* conic,
+                                                        const uint32_t* offsets, const uint4* rec,
                                                         int64_t m, int64_t n, int64_t* status,
                                                         int64_t capacity, Views vs, uint32_t* tkey,
                                                         uint32_t* tval) {
@@ -372,7 +404,7 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     if (wbase < m && total > 0) {
         const uint32_t start = __shfl_sync(0xffffffffu, valid ? offsets[idx] - (incl - cnt) : 0u, 0);
-        const TightLane L = tight_lane_load(cnt ? order[idx] : 0u, cnt != 0u, rect, xy, conic, vs, n);
+        const TightLane L = tight_lane_rec(cnt ? order[idx] : 0u, cnt != 0u, rec, idx, vs, n);
         const uint32_t iw = warp_inclusive_sum(L.wd);
         const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
         const uint32_t ew = iw - L.wd;
@@ -760,6 +792,7 @@ struct SortWs {
     uint32_t* counters;    // tile counter of the running pass (u32 at byte 0 of a 256-B block)
     int64_t* mvis;         // visible entries (int64 at byte 64 of the same block)
     uint32_t* bases;       // [2 * OS_MAX_DIGITS * 256]: digit bases (entry sort, tile sort)
+    uint4* erec;           // [2 * m] tight-box emission records in depth order (see count_tight)
 };
 
 constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -773,7 +806,7 @@ constexpr size_t sort_ws_bytes(int64_t m, int64_t capacity) {
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     const int64_t nt = ceil_div(m > capacity ? m : capacity, OS_TILE);
-    return 6 * align_up(sizeof(uint32_t) * mm) +
+    return 6 * align_up(sizeof(uint32_t) * mm) + align_up(2 * sizeof(uint4) * mm) +
            align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1)) +
            3 * align_up(sizeof(uint32_t) * cap) +
            align_up(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1)) +
@@ -793,6 +826,7 @@ inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws
     char* e3 = take(sizeof(uint32_t) * mm);
     char* e4 = take(sizeof(uint32_t) * mm);
     char* e5 = take(sizeof(uint32_t) * mm);
+    char* er = take(2 * sizeof(uint4) * mm);
     char* p1 = take(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1));
     char* p2 = take(sizeof(uint32_t) * cap);
     char* p3 = take(sizeof(uint32_t) * cap);
@@ -815,6 +849,7 @@ inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws
         ws->counters = reinterpret_cast<uint32_t*>(p7);
         ws->mvis = reinterpret_cast<int64_t*>(p7 + 64);
         ws->bases = reinterpret_cast<uint32_t*>(p8);
+        ws->erec = reinterpret_cast<uint4*>(er);
     }
     return off;
 }
@@ -901,13 +936,13 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
         gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
     else if (vs->tile_w == 16)
         count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
-                                               ws->tiles_s);
+                                               ws->tiles_s, ws->erec);
     else if (vs->tile_w == 8)
         count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
-                                              ws->tiles_s);
+                                              ws->tiles_s, ws->erec);
     else
         count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
-                                              ws->tiles_s);
+                                              ws->tiles_s, ws->erec);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
@@ -919,13 +954,13 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
     if (tight) {
         if (vs->tile_w == 16)
-            emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+            emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
                                                         m, n, d_status, capacity, *vs, ka, va);
         else if (vs->tile_w == 8)
-            emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+            emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
                                                        m, n, d_status, capacity, *vs, ka, va);
         else
-            emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, pxy, pco,
+            emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
                                                        m, n, d_status, capacity, *vs, ka, va);
     } else {
         emit_pairs<<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, m, n, d_status,
