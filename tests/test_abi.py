@@ -74,3 +74,46 @@ def test_selftest_argument_checks_need_no_gpu():
     assert lib.lgs_selftest_wait_timeout(-1, fake, L.SELFTEST_WORKSPACE_BYTES, fake, None) == L.LGS_ERR_ARG
     assert lib.lgs_selftest_wait_timeout(10, ctypes.c_void_p(260), L.SELFTEST_WORKSPACE_BYTES, fake,
                                          None) == L.LGS_ERR_ALIGN
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "lgs.h")).read()
+    out = {}
+    for name, expr in re.findall(r"#define\s+(LGS_\w+)\s+([^/\n]+)", src):
+        expr = re.sub(r"(\d+)(?:ull|ll|u)\b", r"\1", expr.strip())
+        try:
+            out[name] = int(eval(expr, {}))
+        except Exception:
+            pass
+    return out
+
+
+def test_python_constants_match_the_header():
+    d = _header_defines()
+    pairs = {"LGS_ERR_ARG": L.LGS_ERR_ARG, "LGS_ERR_ALIGN": L.LGS_ERR_ALIGN,
+             "LGS_ERR_UNSUPPORTED": L.LGS_ERR_UNSUPPORTED, "LGS_ERR_CAPACITY": L.LGS_ERR_CAPACITY,
+             "LGS_ERR_TIMEOUT": L.LGS_ERR_TIMEOUT, "LGS_ERR_CUDA": L.LGS_ERR_CUDA,
+             "LGS_ERR_INTERNAL": L.LGS_ERR_INTERNAL, "LGS_MAX_VIEWS": L.LGS_MAX_VIEWS,
+             "LGS_SORT_STATIC_MAX_ENTRIES": L.SORT_STATIC_MAX_ENTRIES,
+             "LGS_SORT_STATIC_MAX_INSTANCES": L.SORT_STATIC_MAX_INSTANCES,
+             "LGS_SELFTEST_WORKSPACE_BYTES": L.SELFTEST_WORKSPACE_BYTES,
+             "LGS_STATUS_WORDS": L.LGS_STATUS_WORDS, "LGS_MODE_LOCALGS": L.MODE_LOCALGS,
+             "LGS_MODE_PLAIN": L.MODE_PLAIN, "LGS_MODE_LITERAL": L.MODE_LITERAL,
+             "LGS_MODE_GLOBAL": L.MODE_GLOBAL, "LGS_FLAG_COUNT": L.FLAG_COUNT,
+             "LGS_FLAG_PERSISTENT": L.FLAG_PERSISTENT, "LGS_FLAG_TIGHT": L.FLAG_TIGHT,
+             "LGS_ST_NUM_INSTANCES": L.ST_NUM_INSTANCES, "LGS_ST_PAIRS": L.ST_PAIRS,
+             "LGS_ST_CANDIDATES": L.ST_CANDIDATES}
+    for name, val in pairs.items():
+        assert d[name] == val, name
+
+
+def test_unsupported_staging_batch_is_a_host_error():
+    lib = L.load()
+    cam = (L.lgs_camera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 64, 48, 50.0, 50.0
+    fake = ctypes.c_void_p(16)
+    pre = L.lgs_pre_out(*([16] * 8))
+    for batch in (96, 32, 512, -1):
+        cfg = L.lgs_config(16, 16, 0, batch, 0)   # tile_w, tile_h, mode, batch, flags
+        assert lib.lgs_render_fwd(ctypes.byref(pre), fake, fake, cam, 1, ctypes.byref(cfg), fake, fake,
+                                  fake, fake, None) == L.LGS_ERR_UNSUPPORTED, batch
