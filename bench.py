@@ -227,15 +227,16 @@ class Pipeline:
                             self.d_rgb, None, self.grads, self.status)
 
     def launches(self):
-        """Kernels of one forward step: preprocess; depth keys, digit histogram +
-        bases, 4 entry passes; gather + 3 scan kernels; emission; digit histogram
-        + bases and one onesweep pass per tile-id byte; ranges; render."""
+        """Kernels of one forward step (as in the ncu launch list): preprocess;
+        entry digit histogram + bases, 4 entry passes (the first forms the depth
+        keys); gather or tight count + 3 scan kernels; emission; tile-id digit
+        histogram + bases and one onesweep pass per tile-id byte; ranges; render."""
         nt = self.ranges.shape[0]
         bits = 0
         while (1 << bits) < nt:
             bits += 1
         tile_passes = (bits + 7) // 8
-        return 1 + (1 + 2 + 4) + (1 + 3) + 1 + ((2 + tile_passes) if tile_passes else 0) + 1 + 1
+        return 1 + (2 + 4) + (1 + 3) + 1 + ((2 + tile_passes) if tile_passes else 0) + 1 + 1
 
 
 def time_steps(pipe, cfg, steps, flush, backward=False):
