@@ -123,7 +123,7 @@ typedef struct {
 #define LGS_MODE_GLOBAL 3
 
 #define LGS_FLAG_COUNT 1        /* render also counts its schedule's pixel-Gaussian pairs into d_status[LGS_ST_PAIRS] */
-#define LGS_FLAG_PERSISTENT 2   /* render with persistent CTAs pulling tiles from a work queue */
+#define LGS_FLAG_PERSISTENT 2   /* render and adjoint (LGS_MODE_LOCALGS) with persistent CTAs pulling tiles from a work queue */
 /* Tight-box emission (lgs_sort): an entry is duplicated only into the tiles of
  * its rect that the conservative tight box of Sec. III-C2 reaches, evaluated
  * per tile column strip (the ellipse alpha = 1/255 widened to
@@ -262,7 +262,12 @@ lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* vals, const ui
  * zero), recomputes blending back to front per tile from the stored final_T
  * and n_contrib and accumulates gradients into *grads (caller-zeroed):
  * first the per-(view, Gaussian) 2D gradients, then the chain rule through
- * conic inverse, EWA, covariance, quaternion normalisation and SH. */
+ * conic inverse, EWA, covariance, quaternion normalisation and SH.
+ * cfg->mode LGS_MODE_LOCALGS or LGS_MODE_PLAIN (else LGS_ERR_UNSUPPORTED);
+ * LGS_FLAG_PERSISTENT (Local-GS only) runs the adjoint with persistent CTAs
+ * pulling tiles from the work queue d_status[LGS_ST_QUEUE_BWD]; the gradients
+ * then differ from the one-CTA-per-tile launch only in the order of float
+ * atomics. */
 lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams, int32_t n_views,
                           const lgs_config* cfg, const lgs_pre_out* pre, const uint32_t* vals,
                           const uint32_t* ranges, const float* final_T, const uint32_t* n_contrib,

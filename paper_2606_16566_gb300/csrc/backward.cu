@@ -101,7 +101,7 @@ __device__ __forceinline__ float warp_sum(float x) {
 // writes of the walk (32 lanes, one row) and the 16-B reads of the reduction
 // (8 rows, one column group each) both hit distinct banks.
 constexpr int RED_ROWS = 8;
-struct BwdRed {
+struct __align__(16) BwdRed {
     float dp[RED_ROWS][32];
     float w[RED_ROWS][32];
     uint32_t slot[RED_ROWS];   // batch index of the row's Gaussian
@@ -170,8 +170,10 @@ __device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float
     }
 }
 
+// The adjoint of one tile (every thread of the CTA calls it with the same
+// tile; the shared arrays are the calling kernel's, one set per CTA).
 template <int TW, int TH>
-__global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views vs) {
+__device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, uint32_t tile) {
     __shared__ float4 sV[BWD_BATCH];
     __shared__ float2 sDE[BWD_BATCH];
     __shared__ float4 sC[BWD_BATCH];
@@ -180,11 +182,9 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
     __shared__ uint32_t sId[BWD_BATCH];
     __shared__ float sG[BWD_BATCH][9];
     __shared__ uint32_t sLast[8];
-    __shared__ __align__(16) BwdRed sR[8];
+    __shared__ BwdRed sR[8];
     __shared__ float4 sGp[256];   // (dL/drgb of the thread's pixel, 0)
     static_assert(TW % 8 == 0, "row groups of 8 pixels");
-
-    const uint32_t tile = blockIdx.x;
     const int view = view_of_tile(vs, tile);
     const ViewRec& c = vs.v[view];
     const uint32_t lt = tile - c.tile_off;
@@ -341,6 +341,29 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views 
                 atomicAdd(p.g_rgb + 3 * (int64_t)id + 2, gr2);
             }
         }
+    }
+}
+
+// One CTA per tile.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views vs) {
+    bwd_tile<TW, TH>(p, vs, blockIdx.x);
+}
+
+// Persistent CTAs: each pulls the next tile index from the work-queue counter
+// LGS_ST_QUEUE_BWD (zeroed by the launcher) until all tiles are taken.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256, 5) render_bwd_localgs_persistent(BwdParams p, Views vs) {
+    __shared__ uint32_t s_tile;
+    unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE_BWD);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(q, 1ull);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if (tile >= vs.n_tiles) break;
+        bwd_tile<TW, TH>(p, vs, tile);
+        __syncthreads();
     }
 }
 
@@ -706,9 +729,22 @@ __global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) 
 }
 
 template <int TW, int TH>
-void launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, cudaStream_t s) {
-    if (mode == LGS_MODE_PLAIN) render_bwd_plain<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
-    else render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+lgs_status launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, bool persistent, cudaStream_t s) {
+    if (mode == LGS_MODE_PLAIN) {
+        render_bwd_plain<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+    } else if (!persistent) {
+        render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
+    } else {
+        if (cudaMemsetAsync(bp.status + LGS_ST_QUEUE_BWD, 0, sizeof(int64_t), s) != cudaSuccess)
+            return LGS_ERR_CUDA;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_localgs_persistent<TW, TH>, 256, 0);
+        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+        render_bwd_localgs_persistent<TW, TH><<<g, 256, 0, s>>>(bp, vs);
+    }
+    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace lgs
@@ -758,9 +794,12 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     bp.g_rgb = grads->rgb2d;
     bp.status = d_status;
     if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
-    if (cfg->tile_w == 16) launch_render_bwd<16, 16>(bp, vs, cfg->mode, s);
-    else if (cfg->tile_w == 8) launch_render_bwd<8, 32>(bp, vs, cfg->mode, s);
-    else launch_render_bwd<32, 8>(bp, vs, cfg->mode, s);
+    const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
+    if (persistent && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
+    if (cfg->tile_w == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, persistent, s);
+    else if (cfg->tile_w == 8) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, persistent, s);
+    else st = launch_render_bwd<32, 8>(bp, vs, cfg->mode, persistent, s);
+    if (st != LGS_OK) return st;
     PreBwdParams pp;
     pp.means = g->means; pp.scales = g->scales; pp.quats = g->quats; pp.sh = g->sh; pp.n = g->n;
     pp.conic = reinterpret_cast<const float4*>(pre->conic);

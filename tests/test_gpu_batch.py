@@ -165,3 +165,34 @@ def test_unsupported_staging_batch_is_rejected():
     with pytest.raises(L.LgsError) as e:
         lgs.render_fwd(res["pre"], res["vals"], res["ranges"], cams, lgs.config(batch=96))
     assert e.value.code == L.LGS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("tile", batch.TILE_SHAPES)
+def test_persistent_backward_equals_one_cta_per_tile(tile):
+    """The persistent adjoint (CTAs pulling tiles from the work queue) gives the
+    gradients of the one-CTA-per-tile launch up to the order of float atomics,
+    and leaves the forward outputs bit-identical."""
+    sc, _ = scenes.outdoor(n=30000)
+    cams = _uneven_views(4, seed=12)
+    g = lgs.to_device(sc)
+    rs = [batch.Renderer(g, cams, tile=tile, backward=True, tight=True, persistent=pers)
+          for pers in (False, True)]
+    for r in rs:
+        r.d_rgb.copy_(torch.linspace(-1, 1, r.d_rgb.numel(), device="cuda"))
+        r.forward()
+        r.backward()
+    torch.cuda.synchronize()
+    for r in rs:
+        r.check()
+    for a, b in ((rs[0].rgb, rs[1].rgb), (rs[0].T, rs[1].T), (rs[0].nc, rs[1].nc)):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        d = (rs[0].grads[k] - rs[1].grads[k]).norm() / rs[0].grads[k].norm().clamp_min(1e-30)
+        assert d.item() <= 1e-4, k
+    # the 2D gradients of every (view, Gaussian) entry, summed over its tiles in
+    # another order: sums that cancel lose relative accuracy, so the bound is
+    # relative to the tensor's norm and largest element
+    for k in ("xy2d", "conic2d", "rgb2d"):
+        a, b = rs[0].grads[k], rs[1].grads[k]
+        assert ((a - b).norm() / a.norm().clamp_min(1e-30)).item() <= 1e-5, k
+        assert ((a - b).abs().max() / a.abs().max().clamp_min(1e-30)).item() <= 1e-4, k
