@@ -257,15 +257,18 @@ def test_schedule_pair_count_vs_oracle():
     assert ref <= gpu_pairs <= 1.02 * ref, (gpu_pairs, ref)
 
 
+@pytest.mark.parametrize("tile,tight", [((16, 16), False), ((8, 32), True)])
 @pytest.mark.parametrize("v", [0, 5])
-def test_outdoor_full_size_views(v):
-    """Full outdoor workload (500k Gaussians, 8 views of 1264x832 in one batch,
-    the benchmark's launch configuration); two views checked in full."""
+def test_outdoor_full_size_views(v, tile, tight):
+    """Full outdoor workload (500k Gaussians, 8 views of 1264x832 in one batch);
+    two views checked in full, on 16x16 tiles with full-rect emission and in
+    the benchmark's headline launch configuration (8x32 tiles, tight-box
+    emission, one CTA per tile, 256-Gaussian staging batch)."""
     sc, cams = scenes.outdoor()
     n = sc["means"].shape[0]
-    res = _render(sc, cams)
-    view = to_numpy_view(res, v, cams, n, (16, 16))
-    rep, o = full_view_parity(sc, cams[v], view, (16, 16))
+    res = _render(sc, cams, tile=tile, flags=L.FLAG_TIGHT if tight else 0)
+    view = to_numpy_view(res, v, cams, n, tile)
+    rep, o = full_view_parity(sc, cams[v], view, tile, tight=tight)
     print(rep)
     assert not rep["unexplained_tiles"], rep["unexplained_tiles"][:10]
     assert rep["n_contrib_mismatch"] == 0, rep
