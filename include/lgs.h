@@ -158,7 +158,13 @@ typedef struct {
  *   tiles   [M]   u32 number of tiles in the rect, 0 when culled
  *   rect    [M]   u64 tile rect packed as x_lo | y_lo<<16 | x_hi<<32 | y_hi<<48 (half-open)
  *   flags   [M]   u8  bit c (c<3): colour channel c was clamped at 0;
- *                     bit 3/4: x/z resp. y/z clamped to 1.3 tan(fov/2) in the EWA Jacobian */
+ *                     bit 3/4: x/z resp. y/z clamped to 1.3 tan(fov/2) in the EWA Jacobian
+ *   emit    [M,8] u32 32-B aligned, optional (NULL = not written / not read):
+ *           for visible entries the fields the tight-box emission of lgs_sort
+ *           needs, in one 32-B record: (rect lo32, rect hi32, bits(u_hi + u_lo),
+ *           bits(v_hi + v_lo), bits(a), bits(b), bits(c), bits(o)). lgs_sort with
+ *           LGS_FLAG_TIGHT then gathers one record per entry instead of reading
+ *           rect, xy and conic; results are identical either way. */
 typedef struct {
     float* xy;
     float* conic;
@@ -168,6 +174,7 @@ typedef struct {
     uint32_t* tiles;
     uint64_t* rect;
     uint8_t* flags;
+    uint32_t* emit;
 } lgs_pre_out;
 
 /* Gradients (device, caller-zeroed, accumulated with atomics).

@@ -59,7 +59,7 @@ class lgs_config(ctypes.Structure):
 
 class lgs_pre_out(ctypes.Structure):
     _fields_ = [("xy", _vp), ("conic", _vp), ("rgb", _vp), ("depth", _vp), ("radius", _vp),
-                ("tiles", _vp), ("rect", _vp), ("flags", _vp)]
+                ("tiles", _vp), ("rect", _vp), ("flags", _vp), ("emit", _vp)]
 
 
 class lgs_grads(ctypes.Structure):

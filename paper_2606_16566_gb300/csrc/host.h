@@ -61,6 +61,7 @@ inline lgs_status check_pre(const lgs_pre_out* pre) {
     if (!aligned16(pre->xy) || !aligned16(pre->conic) || !aligned16(pre->rgb))
         return LGS_ERR_ALIGN;
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) != 0) return LGS_ERR_ALIGN;
+    if ((reinterpret_cast<uintptr_t>(pre->emit) & 31u) != 0) return LGS_ERR_ALIGN;
     return LGS_OK;
 }
 

@@ -36,6 +36,7 @@ struct PreParams {
     uint32_t* tiles;
     uint64_t* rect;
     uint8_t* flags;
+    uint4* emit;      // optional emission records (2 x uint4 per entry), may be NULL
     int64_t* status;
 };
 
@@ -221,6 +222,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreParams p, Views vs) 
                 ntiles = area;
                 rpack = (uint64_t)(uint32_t)x0 | ((uint64_t)(uint32_t)y0 << 16) |
                         ((uint64_t)(uint32_t)x1 << 32) | ((uint64_t)(uint32_t)y1 << 48);
+                if (p.emit) {
+                    p.emit[2 * m] = make_uint4((uint32_t)rpack, (uint32_t)(rpack >> 32),
+                                               __float_as_uint(__fadd_rn(u.hi, u.lo)),
+                                               __float_as_uint(__fadd_rn(vv.hi, vv.lo)));
+                    p.emit[2 * m + 1] = make_uint4(__float_as_uint(ca), __float_as_uint(cb),
+                                                   __float_as_uint(cc), __float_as_uint(op));
+                }
             }
         }
         p.radius[m] = rad;
@@ -255,6 +263,7 @@ extern "C" lgs_status lgs_preprocess(const lgs_gaussians* g, const lgs_camera* c
     p.sh = g->sh; p.n = g->n;
     p.xy = out->xy; p.conic = out->conic; p.rgb = out->rgb; p.depth = out->depth;
     p.radius = out->radius; p.tiles = out->tiles; p.rect = out->rect; p.flags = out->flags;
+    p.emit = reinterpret_cast<uint4*>(out->emit);
     p.status = d_status;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     dim3 block(256), grid((unsigned)((p.n + 255) / 256));

@@ -280,14 +280,12 @@ __device__ __forceinline__ TightLane tight_lane_load(uint32_t ent, bool live, co
 // The same lane state from the emission record count_tight left at depth-order
 // index idx ((rect, mean x, mean y), conic: two coalesced 16-B loads instead of
 // a second gather of rect, conic and mean).
-__device__ __forceinline__ TightLane tight_lane_rec(uint32_t ent, bool live, const uint4* rec, int64_t idx,
-                                                    const Views& vs, int64_t n) {
+__device__ __forceinline__ TightLane tight_lane_from(uint32_t ent, bool live, uint4 a, uint4 c,
+                                                     const Views& vs, int64_t n) {
     TightLane L{};
     L.gx = 1;
     L.ent = ent;
     if (live) {
-        const uint4 a = rec[2 * idx];
-        const uint4 c = rec[2 * idx + 1];
         L.x0 = a.x & 0xffffu;
         L.y0 = a.x >> 16;
         L.wd = (a.y & 0xffffu) - L.x0;
@@ -299,6 +297,16 @@ __device__ __forceinline__ TightLane tight_lane_rec(uint32_t ent, bool live, con
                          __uint_as_float(a.z), __uint_as_float(a.w));
     }
     return L;
+}
+
+__device__ __forceinline__ TightLane tight_lane_rec(uint32_t ent, bool live, const uint4* rec, int64_t idx,
+                                                    const Views& vs, int64_t n) {
+    uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
+    if (live) {
+        a = rec[2 * idx];
+        c = rec[2 * idx + 1];
+    }
+    return tight_lane_from(ent, live, a, c, vs, n);
 }
 
 // The tight box of lane `own`'s entry, broadcast to the calling lane.
@@ -345,8 +353,9 @@ __device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t e) {
 template <int TW, int TH>
 __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
                                                    const uint64_t* rect, const float4* xy,
-                                                   const float4* conic, int64_t m, const int64_t* mv,
-                                                   int64_t n, Views vs, uint32_t* tiles_sorted, uint4* rec) {
+                                                   const float4* conic, const uint4* emit, int64_t m,
+                                                   const int64_t* mv, int64_t n, Views vs,
+                                                   uint32_t* tiles_sorted, uint4* rec) {
     __shared__ uint32_t cnt[256];
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
@@ -358,7 +367,21 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
     const uint32_t ent = visible ? order[idx] : 0u;
     // the first entry pass kept only visible entries, so every entry before
     // the visible count has a non-empty rect
-    const TightLane L = tight_lane_load(ent, visible, rect, xy, conic, vs, n, rec, idx);
+    TightLane L;
+    if (emit) {
+        // one 32-B record per entry (written by the preprocess), copied to
+        // the depth-ordered records of the emission
+        uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
+        if (visible) {
+            a = emit[2 * (int64_t)ent];
+            c = emit[2 * (int64_t)ent + 1];
+            rec[2 * idx] = a;
+            rec[2 * idx + 1] = c;
+        }
+        L = tight_lane_from(ent, visible, a, c, vs, n);
+    } else {
+        L = tight_lane_load(ent, visible, rect, xy, conic, vs, n, rec, idx);
+    }
     cnt[threadIdx.x] = 0u;
     __syncwarp();
     const uint32_t iw = warp_inclusive_sum(L.wd);
@@ -931,17 +954,18 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     const bool tight = (vs->flags & LGS_FLAG_TIGHT) != 0;
     const float4* pxy = reinterpret_cast<const float4*>(pre->xy);
     const float4* pco = reinterpret_cast<const float4*>(pre->conic);
+    const uint4* pem = reinterpret_cast<const uint4*>(pre->emit);
     const unsigned eg = (unsigned)ceil_div(m, 256);
     if (!tight)
         gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
     else if (vs->tile_w == 16)
-        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
                                                ws->tiles_s, ws->erec);
     else if (vs->tile_w == 8)
-        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
                                               ws->tiles_s, ws->erec);
     else
-        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, m, ws->mvis, n, *vs,
+        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
                                               ws->tiles_s, ws->erec);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
@@ -1000,6 +1024,7 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
     if ((cfg->flags & LGS_FLAG_TIGHT) && (!pre->xy || !pre->conic)) return LGS_ERR_ARG;
     if ((cfg->flags & LGS_FLAG_TIGHT) && (!aligned16(pre->xy) || !aligned16(pre->conic)))
         return LGS_ERR_ALIGN;
+    if (reinterpret_cast<uintptr_t>(pre->emit) & 31u) return LGS_ERR_ALIGN;
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
         (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;
@@ -1062,6 +1087,7 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
     if ((cfg->flags & LGS_FLAG_TIGHT) && (!pre->xy || !pre->conic)) return LGS_ERR_ARG;
     if ((cfg->flags & LGS_FLAG_TIGHT) && (!aligned16(pre->xy) || !aligned16(pre->conic)))
         return LGS_ERR_ALIGN;
+    if (reinterpret_cast<uintptr_t>(pre->emit) & 31u) return LGS_ERR_ALIGN;
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
         (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;

@@ -86,9 +86,10 @@ class PreOut:
     tiles: torch.Tensor    # [M] i32 storage of u32
     rect: torch.Tensor     # [M] i64 storage of u64
     flags: torch.Tensor    # [M] u8
+    emit: torch.Tensor = None  # [M,8] i32 storage of u32: emission records (optional)
 
     @staticmethod
-    def empty(m, device="cuda"):
+    def empty(m, device="cuda", emit=True):
         f = dict(device=device)
         return PreOut(torch.empty((m, 4), dtype=torch.float32, **f),
                       torch.empty((m, 4), dtype=torch.float32, **f),
@@ -97,17 +98,19 @@ class PreOut:
                       torch.empty(m, dtype=torch.int32, **f),
                       torch.empty(m, dtype=torch.int32, **f),
                       torch.empty(m, dtype=torch.int64, **f),
-                      torch.empty(m, dtype=torch.uint8, **f))
+                      torch.empty(m, dtype=torch.uint8, **f),
+                      torch.empty((m, 8), dtype=torch.int32, **f) if emit else None)
 
     def rows(self, a, b) -> "PreOut":
         """The entries a..b-1 (e.g. the views of a group), as views of the same memory."""
-        return PreOut(*(t[a:b] for t in (self.xy, self.conic, self.rgb, self.depth, self.radius,
-                                          self.tiles, self.rect, self.flags)))
+        return PreOut(*(t[a:b] if t is not None else None
+                        for t in (self.xy, self.conic, self.rgb, self.depth, self.radius, self.tiles,
+                                  self.rect, self.flags, self.emit)))
 
     def struct(self) -> L.lgs_pre_out:
-        return L.lgs_pre_out(*(t.data_ptr() for t in (self.xy, self.conic, self.rgb, self.depth,
-                                                         self.radius, self.tiles, self.rect,
-                                                         self.flags)))
+        return L.lgs_pre_out(*(t.data_ptr() if t is not None else None
+                               for t in (self.xy, self.conic, self.rgb, self.depth, self.radius,
+                                         self.tiles, self.rect, self.flags, self.emit)))
 
 
 def preprocess(g, cams, cfg, out=None, status=None, stream=None) -> PreOut:

@@ -117,3 +117,14 @@ def test_unsupported_staging_batch_is_a_host_error():
         cfg = L.lgs_config(16, 16, 0, batch, 0)   # tile_w, tile_h, mode, batch, flags
         assert lib.lgs_render_fwd(ctypes.byref(pre), fake, fake, cam, 1, ctypes.byref(cfg), fake, fake,
                                   fake, fake, None) == L.LGS_ERR_UNSUPPORTED, batch
+
+
+def test_misaligned_emission_records_are_a_host_error():
+    lib = L.load()
+    cam = (L.lgs_camera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 64, 48, 50.0, 50.0
+    cfg = L.lgs_config(16, 16, 0, 0, 0)
+    fake = ctypes.c_void_p(32)
+    pre = L.lgs_pre_out(*([32] * 8), 48)          # 16-B but not 32-B aligned
+    assert lib.lgs_render_fwd(ctypes.byref(pre), fake, fake, cam, 1, ctypes.byref(cfg), fake, fake,
+                              fake, fake, None) == L.LGS_ERR_ALIGN

@@ -206,3 +206,31 @@ def test_tight_static_sort_equals_workspace_sort():
     torch.testing.assert_close(v2[:K], v1[:K], rtol=0, atol=0)
     torch.testing.assert_close(k2[:K], k1[:K], rtol=0, atol=0)
     torch.testing.assert_close(r2, r1, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_emission_records_of_the_preprocess_change_nothing(tile):
+    """With the preprocess's 32-B emission records (lgs_pre_out.emit) the tight
+    sort gathers one record per entry instead of rect, xy and conic; keys,
+    lists, ranges, counts and images are bit-identical either way."""
+    sc, _ = scenes.outdoor(n=60000)
+    cams = [scenes.look_at((6.0 * np.cos(a), 1.5, 6.0 * np.sin(a)), (0, 0, 0), 640, 416, 60.0)
+            for a in (0.3, 2.1, 4.0)]
+    g = lgs.to_device(sc)
+    n = sc["means"].shape[0]
+    cfg = lgs.config(tile, "localgs", T)
+    outs = []
+    for emit in (True, False):
+        st = lgs.new_status()
+        pre = lgs.preprocess(g, cams, cfg, out=lgs.PreOut.empty(n * len(cams), emit=emit), status=st)
+        assert (pre.emit is not None) == emit
+        cap = 4 * n * len(cams)
+        keys, vals, ranges = lgs.sort(pre, n, cams, cfg, cap, status=st)
+        rgb, T_, nc = lgs.render_fwd(pre, vals, ranges, cams, cfg, status=st)
+        s = lgs.read_status(st)
+        assert s[L.ST_CODE] == 0
+        K = int(s[L.ST_NUM_INSTANCES])
+        outs.append((K, keys[:K].clone(), vals[:K].clone(), ranges.clone(), rgb, T_, nc))
+    assert outs[0][0] == outs[1][0]
+    for a, b in zip(outs[0][1:], outs[1][1:]):
+        assert torch.equal(a, b)
