@@ -74,3 +74,17 @@ def test_traffic_record_is_used_only_for_the_profiled_sources(tmp_path, monkeypa
     assert bench.recorded_traffic("render_localgs_16x16_tight") is None
     (tmp_path / "paper_2606_16566_gb300" / "csrc" / "render.cu").write_bytes(b"// kernel v2\n")
     assert bench.recorded_traffic("render_localgs_8x32_tight") is None
+
+
+def test_preprocess_output_rows_keep_the_abi_alignment():
+    """PreOut.rows (a view group's entries) keeps every array's alignment: 16 B
+    for the float4 arrays, 8 B for rect, 32 B for the emission records."""
+    from paper_2606_16566_gb300 import lgs
+    pre = lgs.PreOut.empty(1000, device="cpu")
+    for a, b in ((0, 1000), (3, 17), (501, 999)):
+        q = pre.rows(a, b)
+        st = q.struct()
+        assert st.xy % 16 == 0 and st.conic % 16 == 0 and st.rgb % 16 == 0
+        assert st.rect % 8 == 0 and st.emit % 32 == 0
+        assert q.emit.shape == (b - a, 8)
+    assert lgs.PreOut.empty(10, device="cpu", emit=False).struct().emit is None
