@@ -21,7 +21,8 @@
  *  - Device pointers are CUDA device addresses on the current device; `stream`
  *    is a cudaStream_t (NULL = legacy default stream). All work is enqueued
  *    asynchronously on that stream; no entry point synchronises except
- *    lgs_read_status. Calls are therefore capturable in a CUDA graph.
+ *    lgs_read_status and lgs_get_device_status. Calls are therefore
+ *    capturable in a CUDA graph.
  *  - Host-checkable errors (NULL pointers, bad sizes, misalignment, unsupported
  *    tile shapes or SH degrees) return a non-zero lgs_status before anything is
  *    enqueued. Errors detected on the device (instance capacity exceeded,
@@ -297,6 +298,13 @@ lgs_status lgs_selftest_wait_timeout(int32_t spin_limit, void* workspace, size_t
 /* Copies the LGS_STATUS_WORDS device status words into h_status after
  * synchronising `stream`. Returns LGS_ERR_CUDA if the copy fails. */
 lgs_status lgs_read_status(const int64_t* d_status, int64_t* h_status, void* stream);
+
+/* The first device-side error of d_status: synchronises `stream` and writes
+ * the code word (LGS_ST_CODE, 0 = none) to *code and its detail word
+ * (LGS_ST_DETAIL, e.g. the capacity the sort needed) to *detail. Either output
+ * pointer may be NULL. Returns LGS_ERR_ARG for a NULL d_status, LGS_ERR_CUDA
+ * if the copy fails. */
+lgs_status lgs_get_device_status(const int64_t* d_status, void* stream, int32_t* code, int64_t* detail);
 
 /* Static description of a status code. */
 const char* lgs_status_string(lgs_status s);

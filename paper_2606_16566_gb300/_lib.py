@@ -90,6 +90,8 @@ SIGNATURES = {
                                         ctypes.POINTER(lgs_grads), _vp, _vp]),
     "lgs_selftest_wait_timeout": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.c_size_t, _vp, _vp]),
     "lgs_read_status": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64), _vp]),
+    "lgs_get_device_status": (ctypes.c_int32, [_vp, _vp, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int64)]),
     "lgs_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "lgs_version": (ctypes.c_int32, []),
 }

@@ -12,6 +12,19 @@ extern "C" lgs_status lgs_read_status(const int64_t* d_status, int64_t* h_status
     return LGS_OK;
 }
 
+extern "C" lgs_status lgs_get_device_status(const int64_t* d_status, void* stream, int32_t* code,
+                                            int64_t* detail) {
+    if (!d_status) return LGS_ERR_ARG;
+    int64_t h[2];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LGS_ERR_CUDA;
+    if (cudaMemcpy(h, d_status + LGS_ST_CODE, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LGS_ERR_CUDA;
+    if (code) *code = (int32_t)h[0];
+    if (detail) *detail = h[1];
+    return LGS_OK;
+}
+
 extern "C" const char* lgs_status_string(lgs_status s) {
     switch (s) {
         case LGS_OK: return "ok";

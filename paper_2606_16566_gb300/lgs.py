@@ -260,6 +260,15 @@ def selftest_wait_timeout(spin_limit=1000, status=None, stream=None) -> np.ndarr
     return read_status(status, stream)
 
 
+def get_device_status(status, stream=None):
+    """(code, detail) of the first device-side error recorded in `status`
+    (lgs_get_device_status; synchronises the stream)."""
+    code, detail = ctypes.c_int32(0), ctypes.c_int64(0)
+    L.check(L.load().lgs_get_device_status(_ptr(status), _stream(stream), ctypes.byref(code),
+                                           ctypes.byref(detail)), "lgs_get_device_status")
+    return int(code.value), int(detail.value)
+
+
 def read_status(status, stream=None) -> np.ndarray:
     h = (ctypes.c_int64 * L.LGS_STATUS_WORDS)()
     L.check(L.load().lgs_read_status(_ptr(status), h, _stream(stream)), "lgs_read_status")

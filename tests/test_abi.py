@@ -128,3 +128,10 @@ def test_misaligned_emission_records_are_a_host_error():
     pre = L.lgs_pre_out(*([32] * 8), 48)          # 16-B but not 32-B aligned
     assert lib.lgs_render_fwd(ctypes.byref(pre), fake, fake, cam, 1, ctypes.byref(cfg), fake, fake,
                               fake, fake, None) == L.LGS_ERR_ALIGN
+
+
+def test_device_status_query_checks_its_arguments():
+    lib = L.load()
+    code = ctypes.c_int32(7)
+    assert lib.lgs_get_device_status(None, None, ctypes.byref(code), None) == L.LGS_ERR_ARG
+    assert code.value == 7

@@ -174,6 +174,8 @@ def test_capacity_overflow_reports_needed_count():
     st = lgs.read_status(status)
     assert st[L.ST_CODE] == L.LGS_ERR_CAPACITY
     assert st[L.ST_DETAIL] == st[L.ST_NUM_INSTANCES] > 10
+    assert lgs.get_device_status(status) == (L.LGS_ERR_CAPACITY, int(st[L.ST_DETAIL]))
+    assert lgs.get_device_status(lgs.new_status()) == (0, 0)
     res = _render(sc, cams)                       # the retry path sizes itself
     assert res["K"] == st[L.ST_DETAIL]
 
