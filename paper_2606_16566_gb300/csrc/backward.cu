@@ -327,12 +327,10 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             const float gdx = co.x * gD + co.y * gE - Dn * gF;
             const float gdy = co.y * gD + co.z * gE - En * gF;
             if (ga != 0.f || gbb != 0.f || gc != 0.f || go != 0.f || gdx != 0.f || gdy != 0.f) {
-                atomicAdd(p.g_conic + 4 * (int64_t)id + 0, ga);
-                atomicAdd(p.g_conic + 4 * (int64_t)id + 1, gbb);
-                atomicAdd(p.g_conic + 4 * (int64_t)id + 2, gc);
-                atomicAdd(p.g_conic + 4 * (int64_t)id + 3, go);
-                atomicAdd(p.g_xy + 2 * (int64_t)id + 0, gdx);
-                atomicAdd(p.g_xy + 2 * (int64_t)id + 1, gdy);
+                // one vector atomic per record (conic2d rows 16-B, xy2d rows
+                // 8-B aligned, checked on the host)
+                atomicAdd(reinterpret_cast<float4*>(p.g_conic) + id, make_float4(ga, gbb, gc, go));
+                atomicAdd(reinterpret_cast<float2*>(p.g_xy) + id, make_float2(gdx, gdy));
             }
             const float gr0 = sG[t][5], gr1 = sG[t][6], gr2 = sG[t][8];
             if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
@@ -767,6 +765,7 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     st = check_pre(pre);
     if (st != LGS_OK) return st;
     if (!grads->xy2d || !grads->conic2d || !grads->rgb2d) return LGS_ERR_ARG;
+    if (!aligned16(grads->conic2d) || (reinterpret_cast<uintptr_t>(grads->xy2d) & 7u)) return LGS_ERR_ALIGN;
     if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
     if (g->n == 0) return LGS_OK;
     if (!g->means || !g->scales || !g->quats || !g->sh || !grads->means || !grads->scales ||
