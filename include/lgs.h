@@ -182,7 +182,8 @@ typedef struct {
  * means [N,3], scales [N,3], quats [N,4], opacities [N], sh [N,(d+1)^2,3].
  * The *_2d buffers are per-(view, Gaussian) scratch gradients of the render
  * stage, M = n_views*N entries: xy2d [M,2] (8-B aligned), conic2d [M,4] (a, b, c, o;
- * 16-B aligned), rgb2d [M,3]; otherwise lgs_render_bwd returns LGS_ERR_ALIGN. */
+ * 16-B aligned), rgb2d [M,4] (r, g, b, unused; 16-B aligned); otherwise
+ * lgs_render_bwd returns LGS_ERR_ALIGN. */
 typedef struct {
     float* means;
     float* scales;

@@ -107,7 +107,7 @@ class Renderer:
             if backward:
                 part["d_rgb"] = self.d_rgb[3 * poff:3 * (poff + npx)]
                 part["grads"] = dict(self.grads)
-                for k, w in (("xy2d", 2), ("conic2d", 4), ("rgb2d", 3)):
+                for k, w in (("xy2d", 2), ("conic2d", 4), ("rgb2d", 4)):
                     part["grads"][k] = self.grads[k][v0 * self.n:v1 * self.n]
             self.parts.append(part)
             voff, toff, poff = voff + cap, toff + nt, poff + npx

@@ -52,7 +52,7 @@ struct BwdParams {
     const float* dL_dT;
     float* g_xy;      // [M,2]
     float* g_conic;   // [M,4]
-    float* g_rgb;     // [M,3]
+    float* g_rgb;     // [M,4] (r, g, b, unused), 16-B rows
     int64_t* status;
 };
 
@@ -334,9 +334,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             }
             const float gr0 = sG[t][5], gr1 = sG[t][6], gr2 = sG[t][8];
             if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 0, gr0);
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 1, gr1);
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 2, gr2);
+                atomicAdd(reinterpret_cast<float4*>(p.g_rgb) + id, make_float4(gr0, gr1, gr2, 0.f));
             }
         }
     }
@@ -493,9 +491,9 @@ __global__ void __launch_bounds__(256) render_bwd_plain(BwdParams p, Views vs) {
                 atomicAdd(p.g_xy + 2 * (int64_t)id + 1, sG[t][4]);
             }
             if (sG[t][6] != 0.f || sG[t][7] != 0.f || sG[t][8] != 0.f) {
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 0, sG[t][6]);
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 1, sG[t][7]);
-                atomicAdd(p.g_rgb + 3 * (int64_t)id + 2, sG[t][8]);
+                atomicAdd(p.g_rgb + 4 * (int64_t)id + 0, sG[t][6]);
+                atomicAdd(p.g_rgb + 4 * (int64_t)id + 1, sG[t][7]);
+                atomicAdd(p.g_rgb + 4 * (int64_t)id + 2, sG[t][8]);
             }
         }
     }
@@ -594,7 +592,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) 
         const uint8_t fl = p.flags[m];
         // ---- colour
         {
-            float gcol[3] = {p.g_rgb[3 * m], p.g_rgb[3 * m + 1], p.g_rgb[3 * m + 2]};
+            float gcol[3] = {p.g_rgb[4 * m], p.g_rgb[4 * m + 1], p.g_rgb[4 * m + 2]};
             float d0 = mx - c.campos[0], d1 = my - c.campos[1], d2 = mz - c.campos[2];
             const float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
             const float id = 1.f / dn;
@@ -765,7 +763,8 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     st = check_pre(pre);
     if (st != LGS_OK) return st;
     if (!grads->xy2d || !grads->conic2d || !grads->rgb2d) return LGS_ERR_ARG;
-    if (!aligned16(grads->conic2d) || (reinterpret_cast<uintptr_t>(grads->xy2d) & 7u)) return LGS_ERR_ALIGN;
+    if (!aligned16(grads->conic2d) || !aligned16(grads->rgb2d) || (reinterpret_cast<uintptr_t>(grads->xy2d) & 7u))
+        return LGS_ERR_ALIGN;
     if (reinterpret_cast<uintptr_t>(ranges) & 7u) return LGS_ERR_ALIGN;
     if (g->n == 0) return LGS_OK;
     if (!g->means || !g->scales || !g->quats || !g->sh || !grads->means || !grads->scales ||
@@ -776,7 +775,7 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     const int64_t m = g->n * (int64_t)n_views;
     if (cudaMemsetAsync(grads->xy2d, 0, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess ||
         cudaMemsetAsync(grads->conic2d, 0, sizeof(float) * 4 * (size_t)m, s) != cudaSuccess ||
-        cudaMemsetAsync(grads->rgb2d, 0, sizeof(float) * 3 * (size_t)m, s) != cudaSuccess)
+        cudaMemsetAsync(grads->rgb2d, 0, sizeof(float) * 4 * (size_t)m, s) != cudaSuccess)
         return LGS_ERR_CUDA;
     BwdParams bp;
     bp.xy = reinterpret_cast<const float4*>(pre->xy);

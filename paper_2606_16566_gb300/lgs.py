@@ -202,7 +202,7 @@ def new_grads(g, n_views):
     z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=dev)
     return {"means": z(g["means"].shape), "scales": z(g["scales"].shape), "quats": z(g["quats"].shape),
             "opacities": z(g["opacities"].shape), "sh": z(g["sh"].shape),
-            "xy2d": z((m, 2)), "conic2d": z((m, 4)), "rgb2d": z((m, 3))}
+            "xy2d": z((m, 2)), "conic2d": z((m, 4)), "rgb2d": z((m, 4))}
 
 
 def render_bwd(g, cams, cfg, pre: PreOut, vals, ranges, final_T, n_contrib, dL_drgb, dL_dT=None,

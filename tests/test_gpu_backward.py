@@ -49,7 +49,7 @@ def test_backward_matches_oracle_adjoint(tile, deg, mode):
         "uv": _rel(gg["xy2d"], g2[:, 0:2]),
         "conic": _rel(gg["conic2d"][:, :3], g2[:, 2:5]),
         "opac2d": _rel(gg["conic2d"][:, 3], g2[:, 5]),
-        "rgb2d": _rel(gg["rgb2d"], g2[:, 6:9]),
+        "rgb2d": _rel(gg["rgb2d"][:, :3], g2[:, 6:9]),
     }
     for k in ("means", "scales", "quats", "opacities", "sh"):
         rep[k] = _rel(gg[k], ref[k])
