@@ -239,9 +239,16 @@ lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_camera* cams, i
  * LGS_SORT_STATIC_MAX_INSTANCES, otherwise LGS_ERR_UNSUPPORTED is returned
  * before anything is enqueued. Other arguments, outputs and errors are those of
  * lgs_sort.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the one array, which keeps the previous call's
+ * The array belongs to the library's sort module: with CUDA's lazy module
+ * loading (the default) that module, and with it the array, is loaded on a
+ * device by the first call of any sort entry point there (lgs_sort,
+ * lgs_sort_static or lgs_selftest_wait_timeout). The first lgs_sort_static
+ * call on a device also looks up the array's device address (once per device,
+ * with that device current) and caches it for the life of the process. Make a
+ * first sort call on each device before any stream capture. The cached address
+ * belongs to the device's primary context: resetting the device
+ * (cudaDeviceReset) or making another context current on it between calls is
+ * not supported. All calls share the one array, which keeps the previous call's
  * contents (nothing in it needs to start at zero: every word the sort reads is
  * written earlier in the same call), so calls whose work overlaps on the GPU
  * (other streams, other host threads) race and must be serialised by the
@@ -296,6 +303,22 @@ lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* cams, int32_
 #define LGS_SELFTEST_WORKSPACE_BYTES (256ull << 10)
 lgs_status lgs_selftest_wait_timeout(int32_t spin_limit, void* workspace, size_t workspace_bytes,
                                      int64_t* d_status, void* stream);
+
+/* Throughput probe of one SM pipe (a measurement utility; no counterpart in
+ * the paper): enqueues `blocks` CTAs of 256 threads, each thread running 8
+ * independent chains of 16 * iters dependent operations of the chosen kind,
+ * and writes the operation count of the launch to *ops (host): FP32 flops for
+ * LGS_PROBE_FFMA (scalar fused multiply-add, 2 flops each) and LGS_PROBE_FFMA2
+ * (packed fma.rn.f32x2, 4 flops each), ex2.approx results for LGS_PROBE_EX2.
+ * Dividing *ops by the launch's duration (caller-timed, e.g. CUDA events on
+ * `stream`) gives the pipe's throughput at the clock the GPU ran at. d_sink
+ * (device, >= blocks floats) only keeps the chains live; it is practically
+ * never written. */
+#define LGS_PROBE_FFMA 0
+#define LGS_PROBE_FFMA2 1
+#define LGS_PROBE_EX2 2
+lgs_status lgs_peak_probe(int32_t kind, int32_t blocks, int32_t iters, float* d_sink, double* ops,
+                          void* stream);
 
 /* Copies the LGS_STATUS_WORDS device status words into h_status after
  * synchronising `stream`. Returns LGS_ERR_CUDA if the copy fails. */

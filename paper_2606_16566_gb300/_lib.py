@@ -35,6 +35,7 @@ MODE_GLOBAL = 3
 FLAG_COUNT = 1
 FLAG_PERSISTENT = 2
 FLAG_TIGHT = 4
+PROBE_FFMA, PROBE_FFMA2, PROBE_EX2 = 0, 1, 2
 
 _vp = ctypes.c_void_p
 
@@ -92,6 +93,8 @@ SIGNATURES = {
     "lgs_read_status": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64), _vp]),
     "lgs_get_device_status": (ctypes.c_int32, [_vp, _vp, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int64)]),
+    "lgs_peak_probe": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                        ctypes.POINTER(ctypes.c_double), _vp]),
     "lgs_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "lgs_version": (ctypes.c_int32, []),
 }

@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblgs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["preprocess.cu", "sort.cu", "render.cu", "backward.cu", "api.cu"]
+SOURCES = ["preprocess.cu", "sort.cu", "render.cu", "backward.cu", "api.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreParams p, Views vs) 
                    (1.f - 2.f * (x * x + y * y)) * sz};
 
     float shc[NC];
-    bool sh_loaded = false;
+    bool sh_loaded = false, sh_ok = true;
 
     for (int v = 0; v < vs.n; ++v) {
         const ViewRec& c = vs.v[v];
@@ -204,7 +204,19 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreParams p, Views vs) 
                         for (int k = 0; k < NC; ++k) shc[k] = src[k];
                     }
                     sh_loaded = true;
+                    // a non-finite SH coefficient culls the Gaussian in this
+                    // and every later view (earlier views reached no tile, so
+                    // it was culled there anyway) and is counted once; SH is
+                    // read, and so checked, only for Gaussians that reach a tile
+                    float probe = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) probe = __fadd_rn(probe, __fmul_rn(shc[k], 0.f));
+                    sh_ok = probe == 0.f;
+                    if (!sh_ok)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_NONFINITE), 1ull);
                 }
+            }
+            if (area > 0 && sh_ok) {
                 float dx = mx - c.campos[0], dy = my - c.campos[1], dzz = mz - c.campos[2];
                 const float inv = 1.f / sqrtf(dx * dx + dy * dy + dzz * dzz);
                 dx *= inv; dy *= inv; dzz *= inv;

@@ -822,59 +822,61 @@ constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Bytes of the sort workspace for m entries and an instance capacity
-// (usable in constant expressions).
-constexpr size_t sort_ws_bytes(int64_t m, int64_t capacity) {
+// Byte offsets of the workspace buffers for m entries and an instance
+// capacity. One constexpr function is the only description of the layout: the
+// workspace query, the carving of a caller's buffer and the compile-time check
+// of the static scratch array all read it.
+struct SortWsOffsets {
+    size_t ek, ev, ek2, ev2, tiles_s, offsets, erec, block_sums, ak, bk, bv, look, counters, bases;
+    size_t total;
+};
+
+constexpr SortWsOffsets sort_ws_offsets(int64_t m, int64_t capacity) {
     const size_t mm = (size_t)(m > 0 ? m : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     const int64_t nt = ceil_div(m > capacity ? m : capacity, OS_TILE);
-    return 6 * align_up(sizeof(uint32_t) * mm) + align_up(2 * sizeof(uint4) * mm) +
-           align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1)) +
-           3 * align_up(sizeof(uint32_t) * cap) +
-           align_up(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1)) +
-           align_up(8 * sizeof(uint32_t)) + align_up(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
+    SortWsOffsets o{};
+    size_t off = 0;
+    o.ek = off;         off += align_up(sizeof(uint32_t) * mm);
+    o.ev = off;         off += align_up(sizeof(uint32_t) * mm);
+    o.ek2 = off;        off += align_up(sizeof(uint32_t) * mm);
+    o.ev2 = off;        off += align_up(sizeof(uint32_t) * mm);
+    o.tiles_s = off;    off += align_up(sizeof(uint32_t) * mm);
+    o.offsets = off;    off += align_up(sizeof(uint32_t) * mm);
+    o.erec = off;       off += align_up(2 * sizeof(uint4) * mm);
+    o.block_sums = off; off += align_up(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1));
+    o.ak = off;         off += align_up(sizeof(uint32_t) * cap);
+    o.bk = off;         off += align_up(sizeof(uint32_t) * cap);
+    o.bv = off;         off += align_up(sizeof(uint32_t) * cap);
+    o.look = off;       off += align_up(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1));
+    o.counters = off;   off += align_up(8 * sizeof(uint32_t));
+    o.bases = off;      off += align_up(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
+    o.total = off;
+    return o;
 }
 
+// Carves the workspace at `base` (256-B aligned) into *ws; returns its size.
 inline size_t sort_ws_layout(int64_t m, int64_t capacity, char* base, SortWs* ws) {
-    const size_t mm = (size_t)(m > 0 ? m : 1);
-    const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
-    const int64_t nscan = ceil_div(m, SCAN_TILE);
-    const int64_t nt = ceil_div(m > capacity ? m : capacity, OS_TILE);
-    size_t off = 0;
-    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align_up(bytes); return p; };
-    char* e0 = take(sizeof(uint32_t) * mm);
-    char* e1 = take(sizeof(uint32_t) * mm);
-    char* e2 = take(sizeof(uint32_t) * mm);
-    char* e3 = take(sizeof(uint32_t) * mm);
-    char* e4 = take(sizeof(uint32_t) * mm);
-    char* e5 = take(sizeof(uint32_t) * mm);
-    char* er = take(2 * sizeof(uint4) * mm);
-    char* p1 = take(sizeof(uint64_t) * (size_t)(nscan > 0 ? nscan : 1));
-    char* p2 = take(sizeof(uint32_t) * cap);
-    char* p3 = take(sizeof(uint32_t) * cap);
-    char* p4 = take(sizeof(uint32_t) * cap);
-    char* p6 = take(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1));
-    char* p7 = take(8 * sizeof(uint32_t));
-    char* p8 = take(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
-    if (ws) {
-        ws->ek = reinterpret_cast<uint32_t*>(e0);
-        ws->ev = reinterpret_cast<uint32_t*>(e1);
-        ws->ek2 = reinterpret_cast<uint32_t*>(e2);
-        ws->ev2 = reinterpret_cast<uint32_t*>(e3);
-        ws->tiles_s = reinterpret_cast<uint32_t*>(e4);
-        ws->offsets = reinterpret_cast<uint32_t*>(e5);
-        ws->block_sums = reinterpret_cast<uint64_t*>(p1);
-        ws->ak = reinterpret_cast<uint32_t*>(p2);
-        ws->bk = reinterpret_cast<uint32_t*>(p3);
-        ws->bv = reinterpret_cast<uint32_t*>(p4);
-        ws->look = reinterpret_cast<unsigned long long*>(p6);
-        ws->counters = reinterpret_cast<uint32_t*>(p7);
-        ws->mvis = reinterpret_cast<int64_t*>(p7 + 64);
-        ws->bases = reinterpret_cast<uint32_t*>(p8);
-        ws->erec = reinterpret_cast<uint4*>(er);
+    const SortWsOffsets o = sort_ws_offsets(m, capacity);
+    if (ws && base) {
+        ws->ek = reinterpret_cast<uint32_t*>(base + o.ek);
+        ws->ev = reinterpret_cast<uint32_t*>(base + o.ev);
+        ws->ek2 = reinterpret_cast<uint32_t*>(base + o.ek2);
+        ws->ev2 = reinterpret_cast<uint32_t*>(base + o.ev2);
+        ws->tiles_s = reinterpret_cast<uint32_t*>(base + o.tiles_s);
+        ws->offsets = reinterpret_cast<uint32_t*>(base + o.offsets);
+        ws->erec = reinterpret_cast<uint4*>(base + o.erec);
+        ws->block_sums = reinterpret_cast<uint64_t*>(base + o.block_sums);
+        ws->ak = reinterpret_cast<uint32_t*>(base + o.ak);
+        ws->bk = reinterpret_cast<uint32_t*>(base + o.bk);
+        ws->bv = reinterpret_cast<uint32_t*>(base + o.bv);
+        ws->look = reinterpret_cast<unsigned long long*>(base + o.look);
+        ws->counters = reinterpret_cast<uint32_t*>(base + o.counters);
+        ws->mvis = reinterpret_cast<int64_t*>(base + o.counters + 64);
+        ws->bases = reinterpret_cast<uint32_t*>(base + o.bases);
     }
-    return off;
+    return o.total;
 }
 
 inline int tile_passes(uint32_t n_tiles) {
@@ -1045,7 +1047,7 @@ extern "C" lgs_status lgs_sort(const lgs_pre_out* pre, int64_t n, const lgs_came
 // library holds LGS_SORT_STATIC_BYTES of it until the process exits.
 namespace lgs {
 constexpr size_t kSortStaticBytes =
-    sort_ws_bytes(LGS_SORT_STATIC_MAX_ENTRIES, LGS_SORT_STATIC_MAX_INSTANCES);
+    sort_ws_offsets(LGS_SORT_STATIC_MAX_ENTRIES, LGS_SORT_STATIC_MAX_INSTANCES).total;
 static_assert(kSortStaticBytes <= (size_t)LGS_SORT_STATIC_BYTES,
               "LGS_SORT_STATIC_BYTES must cover the workspace at the stated maxima");
 }  // namespace lgs
@@ -1091,6 +1093,10 @@ extern "C" lgs_status lgs_sort_static(const lgs_pre_out* pre, int64_t n, const l
     if ((reinterpret_cast<uintptr_t>(pre->rect) & 7u) || (reinterpret_cast<uintptr_t>(keys) & 7u) ||
         (reinterpret_cast<uintptr_t>(ranges) & 7u))
         return LGS_ERR_ALIGN;
+    // the layout at these sizes must fit the array (it does whenever the
+    // limits above hold; the check guards against a later layout change)
+    if (sort_ws_layout(m, capacity, nullptr, nullptr) > (size_t)LGS_SORT_STATIC_BYTES)
+        return LGS_ERR_INTERNAL;
     void* scratch = nullptr;
     st = sort_static_scratch(&scratch);
     if (st != LGS_OK) return st;

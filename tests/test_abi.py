@@ -66,6 +66,17 @@ def test_host_side_argument_checks_need_no_gpu():
     assert pre.xy is None
 
 
+def test_peak_probe_argument_checks_need_no_gpu():
+    lib = L.load()
+    ops = ctypes.c_double(0.0)
+    fake = ctypes.c_void_p(256)
+    assert lib.lgs_peak_probe(L.PROBE_FFMA, 0, 10, fake, ctypes.byref(ops), None) == L.LGS_ERR_ARG
+    assert lib.lgs_peak_probe(L.PROBE_FFMA, 4, 10, None, ctypes.byref(ops), None) == L.LGS_ERR_ARG
+    assert lib.lgs_peak_probe(L.PROBE_EX2, 4, 0, fake, ctypes.byref(ops), None) == L.LGS_ERR_ARG
+    assert lib.lgs_peak_probe(9, 4, 10, fake, ctypes.byref(ops), None) == L.LGS_ERR_UNSUPPORTED
+    assert ops.value == 0.0
+
+
 def test_selftest_argument_checks_need_no_gpu():
     lib = L.load()
     assert lib.lgs_selftest_wait_timeout(10, None, 0, None, None) == L.LGS_ERR_ARG
@@ -102,7 +113,8 @@ def test_python_constants_match_the_header():
              "LGS_MODE_GLOBAL": L.MODE_GLOBAL, "LGS_FLAG_COUNT": L.FLAG_COUNT,
              "LGS_FLAG_PERSISTENT": L.FLAG_PERSISTENT, "LGS_FLAG_TIGHT": L.FLAG_TIGHT,
              "LGS_ST_NUM_INSTANCES": L.ST_NUM_INSTANCES, "LGS_ST_PAIRS": L.ST_PAIRS,
-             "LGS_ST_CANDIDATES": L.ST_CANDIDATES}
+             "LGS_ST_CANDIDATES": L.ST_CANDIDATES, "LGS_PROBE_FFMA": L.PROBE_FFMA,
+             "LGS_PROBE_FFMA2": L.PROBE_FFMA2, "LGS_PROBE_EX2": L.PROBE_EX2}
     for name, val in pairs.items():
         assert d[name] == val, name
 

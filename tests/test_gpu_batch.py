@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2606_16566_gb300 import batch, lgs, scenes
 from paper_2606_16566_gb300 import _lib as L
 
@@ -107,6 +108,35 @@ def test_batched_64_uneven_views_graph_fwd_bwd(tile, persistent, tight):
         assert_image_parity(rep, f"batched view {v}")
     for k in ("means", "scales", "quats", "opacities", "sh"):
         assert torch.isfinite(r.grads[k]).all(), k
+    # Gradients at full size, through the same graph: the upstream gradient is
+    # non-zero only in a 64x64 window (aligned to the tile grid) of views 0 and
+    # 37, so the exact gradients involve only those pixels, and the oracle
+    # computes them on a camera cropped to each window (the same tile lists
+    # inside it). Each 3D gradient tensor is compared with the sum of the two
+    # oracle adjoints, <= 1e-3 relative per tensor.
+    win = 64
+    rng = np.random.default_rng(23)
+    d_rgb = torch.zeros_like(r.d_rgb)
+    views = lgs.split_views(d_rgb, cams, 3)
+    ref = None
+    for v in (0, 37):
+        c = cams[v]
+        x0 = (c["width"] // 2) // 32 * 32
+        y0 = (c["height"] // 2) // 32 * 32
+        w = rng.standard_normal((3, win, win)).astype(np.float32)
+        views[v][:, y0:y0 + win, x0:x0 + win] = torch.from_numpy(w).cuda()
+        one = oracle.backward(sc, scenes.crop_camera(c, x0, y0, win, win), w, None, tile[0], tile[1])
+        ref = one if ref is None else {k: ref[k] + one[k] for k in ref}
+    r.d_rgb.copy_(d_rgb)
+    r.step()
+    torch.cuda.synchronize()
+    r.check()
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        got = r.grads[k].double().cpu().numpy().reshape(-1)
+        exp = ref[k].reshape(-1)
+        rel = np.linalg.norm(got - exp) / max(np.linalg.norm(exp), 1e-30)
+        print("window gradients", k, rel)
+        assert rel <= 1e-3, (k, rel)
 
 
 def test_view_groups_change_no_output():

@@ -76,11 +76,16 @@ def test_checked_build_catches_a_corrupted_tile_range(libs):
     g = lgs.to_device(sc)
     res = lgs.render(g, cams)
     K = res["K"]
+    assert K > 0
+    # The corrupted range ends 1000 entries past the K sorted instances. The
+    # value buffer is extended by 1000 copies of a valid entry index, so even a
+    # build without the check would read only allocated, valid records.
+    vals = torch.cat([res["vals"], res["vals"][:1].expand(1000)]).contiguous()
     ranges = res["ranges"].clone()
     ranges[0, 0] = 0
     ranges[0, 1] = K + 1000                          # past the sorted instances
     st = lgs.new_status()
     st[L.ST_NUM_INSTANCES] = K                       # the sort's status words
-    rgb, T, nc = lgs.render_fwd(res["pre"], res["vals"], ranges, cams, res["cfg"], status=st)
+    rgb, T, nc = lgs.render_fwd(res["pre"], vals, ranges, cams, res["cfg"], status=st)
     s = lgs.read_status(st)
     assert s[L.ST_CODE] == L.LGS_ERR_INTERNAL and s[L.ST_DETAIL] == 1020

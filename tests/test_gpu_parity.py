@@ -45,14 +45,19 @@ def test_preprocess_matches_oracle(seed, deg):
 
 def test_preprocess_culls_and_counts_nonfinite():
     sc, cams = scenes.random_small(64, seed=5)
+    clean = _render(sc, cams)["pre"].tiles.cpu().numpy()
+    # a Gaussian that reaches a tile (its SH is read, and so checked, only then)
+    k = next(i for i in range(10, 64) if clean[i] > 0)
     sc["means"][3] = [np.nan, 0, 0]
     sc["scales"][7, 1] = np.inf
     sc["means"][9] = [0.0, 0.0, -10.0]        # behind the camera
+    sc["sh"][k, 0, 1] = np.nan
     res = _render(sc, cams)
     st = lgs.read_status(res["status"])
-    assert st[L.ST_NONFINITE] == 2
+    assert st[L.ST_NONFINITE] == 3
     tiles = res["pre"].tiles.cpu().numpy()
-    assert tiles[3] == 0 and tiles[7] == 0 and tiles[9] == 0
+    assert tiles[3] == 0 and tiles[7] == 0 and tiles[9] == 0 and tiles[k] == 0
+    assert np.isfinite(res["rgb_flat"].cpu().numpy()).all()
 
 
 # --------------------------------------------------------------------------- sort
@@ -101,7 +106,8 @@ def test_sort_bitexact_against_host_stable_sort(tile):
 
 
 def test_sort_many_instances_multi_pass():
-    """Enough instances for many 4096-pair blocks of the tile passes."""
+    """Enough instances (> 50k) for many blocks of every radix pass, entry
+    passes and tile-id passes alike, so the look-back chains span many blocks."""
     sc, cams = scenes.random_small(20000, seed=10, width=640, height=480, log_scale_mean=-2.5)
     res = _render(sc, cams)
     k = res["keys"].cpu().numpy().view(np.uint64)
@@ -114,8 +120,9 @@ def test_sort_many_instances_multi_pass():
 
 @pytest.mark.parametrize("n,W,H", [(6000, 64, 48), (30000, 96, 64)])
 def test_sort_large_tile_segments(n, W, H):
-    """Large overlapping Gaussians in a small image: tile segments of several
-    thousand instances take the chunked global-memory segment sort."""
+    """Large overlapping Gaussians in a small image: single tiles hold several
+    thousand instances, so one tile's list spans more than one radix block and
+    the depth order inside it must survive the block boundaries."""
     sc, cams = scenes.random_small(n, seed=12, width=W, height=H, log_scale_mean=-1.3,
                                    log_scale_std=0.3)
     res = _render(sc, cams)

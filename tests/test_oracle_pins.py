@@ -406,3 +406,87 @@ def test_fp32_local_frame_error_within_printed_bound():
     xl, ml = x - T, mu - T
     loc = xl * xl - f32(2) * ml * xl + ml * ml
     assert np.max(np.abs(loc.astype(np.float64) - exact)) <= 4 * 32 ** 2 * eps
+
+
+# --------------------------------------------------------------------------- near plane
+def test_near_plane_cull_at_0p2_inclusive():
+    """D3: a Gaussian whose camera-space z is <= 0.2 is culled (radius 0, no
+    tiles); one just beyond is kept. The means are given as exact doubles, so z
+    = 0.2 reaches the comparison unrounded and '<' in place of '<=' (or another
+    constant) fails."""
+    cam = _axis_camera(63, 63, 100.0)
+    zs = [0.19, 0.2, 0.2 * (1 + 1e-12), 0.21]
+    n = len(zs)
+    sc = {"means": np.array([[0.0, 0.0, z] for z in zs]), "scales": np.full((n, 3), 1e-3),
+          "quats": np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), "opacities": np.full(n, 0.8),
+          "sh": np.full((n, 1, 3), 0.3)}
+    pre = oracle.preprocess(sc, cam, exact=True)
+    np.testing.assert_array_equal(pre["radius"] > 0, [False, False, True, True])
+    np.testing.assert_array_equal(pre["tiles"] > 0, [False, False, True, True])
+    np.testing.assert_array_equal(pre["depth"], zs)
+    # the cull decision at exactly 0.2 lies in the near-plane guard band
+    assert pre["gflags"][1] & oracle.GF_NEAR
+    assert not pre["gflags"][3] & oracle.GF_NEAR
+
+
+# --------------------------------------------------------------------------- Local-GS work count
+def test_localgs_pairs_single_gaussian_equals_row_intersections():
+    """Without a stop, the pair count of one Gaussian is, per tile of its list,
+    the number of 16x2 warp strips whose integer rows meet its alpha = 1/255
+    ellipse inside the tile column (brute force over rows, as in the warp-mask
+    pin), times the 32 pixels of a strip."""
+    rng = np.random.default_rng(61)
+    cam = _axis_camera(96, 96, 100.0)
+    checked = 0
+    for trial in range(40):
+        z = 4.0
+        s = rng.uniform(0.02, 0.12, 3)
+        q = rng.standard_normal(4)
+        mx, my = rng.uniform(-1.0, 1.0, 2)
+        o = rng.uniform(0.05, 0.6)
+        sc = _scene([[mx, my, z]], [s], [q], [o], [[[0.2, 0.2, 0.2]]])
+        r = oracle.render(sc, cam)
+        pre = r["pre"]
+        a, b, c = pre["conic"][0]
+        ou = float(np.float32(o))
+        tau = 2 * math.log(255 * ou)
+        mux, muy = pre["uv"][0]
+        ref = 0
+        ambiguous = False
+        gx = 6
+        for t in range(gx * gx):
+            st, en = r["ranges"][t]
+            if en <= st:
+                continue
+            X0, Y0 = (t % gx) * 16, (t // gx) * 16
+            for w in range(8):
+                hit = any(_row_hits(a, b, c, tau, X0 - mux, X0 + 15 - mux, Y0 + 2 * w + k - muy)
+                          for k in range(2))
+                hit_eps = [any(_row_hits(a, b, c, tau, X0 - mux, X0 + 15 - mux, Y0 + 2 * w + k + e - muy)
+                               for k in range(2)) for e in (-1e-7, 1e-7)]
+                ambiguous |= hit_eps[0] != hit or hit_eps[1] != hit
+                ref += 32 * hit
+        if ambiguous or tau <= 0:
+            continue
+        assert r["stop_pos"].max() == 0
+        assert oracle.localgs_pairs(r, cam) == ref, trial
+        checked += 1
+    assert checked >= 30
+
+
+def test_localgs_pairs_stop_at_the_warps_last_stop_position():
+    """A stack of five wide alpha ~ 0.95 Gaussians over a single 16x16 tile:
+    every pixel stops at list position 4 (T: 1 -> ~0.05 -> ~2.5e-3 -> ~1.3e-4,
+    then T(1 - alpha) < 1e-4), so each of the 8 warps is counted for exactly
+    the first 4 Gaussians of the list: 8 x 4 x 32 = 1024 pairs, not the
+    5 x 256 = 1280 of the whole list."""
+    cam = _axis_camera(16, 16, 100.0)
+    n = 5
+    depths = [2.0 + 0.5 * k for k in range(n)]
+    sc = _scene([[0, 0, d] for d in depths], [[1.0] * 3] * n, [[1, 0, 0, 0]] * n, [0.95] * n,
+                [[[0.1 * k, 0.1, 0.1]] for k in range(n)])
+    r = oracle.render(sc, cam)
+    assert np.all(r["stop_pos"] == 4)
+    assert np.all(r["n_contrib"] == 3)
+    assert r["ranges"][0][1] - r["ranges"][0][0] == n
+    assert oracle.localgs_pairs(r, cam) == 8 * 4 * 32

@@ -64,7 +64,8 @@ def test_static_sort_refuses_sizes_beyond_its_maximum():
     lib = L.load()
     ps = pre.struct()
     carr = lgs.cameras(cams)
-    buf = torch.empty(16, dtype=torch.int64, device="cuda")
+    sentinel = 0x5A5A5A5A5A5A5A5A
+    buf = torch.full((16,), sentinel, dtype=torch.int64, device="cuda")
     p = ctypes.c_void_p(buf.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     too_many = L.SORT_STATIC_MAX_INSTANCES + 1
@@ -73,4 +74,7 @@ def test_static_sort_refuses_sizes_beyond_its_maximum():
     too_many_entries = L.SORT_STATIC_MAX_ENTRIES + 1
     assert lib.lgs_sort_static(ctypes.byref(ps), too_many_entries, carr, 1, ctypes.byref(cfg), 1024,
                                p, p, p, p, stream) == L.LGS_ERR_UNSUPPORTED
-    assert np.all(buf.cpu().numpy() == buf.cpu().numpy())
+    # a refused call returns before enqueuing anything: the buffer it was
+    # handed for keys, values, ranges and status still holds the sentinel
+    torch.cuda.synchronize()
+    assert np.all(buf.cpu().numpy() == sentinel)
