@@ -2,19 +2,25 @@
 
 Workload (outdoor scene): 500,000 Gaussians FP32 with SH degree 3 drawn from 64
 anisotropic clusters plus a 10 % background shell at radius 10, seen by 8
-orbit cameras at 1264x832 (16x16 tiles). One step renders all 8 views through
-the whole hot path: preprocess -> scan/emit/radix sort/ranges -> render, in
-one batched launch per stage. ``value`` is frames (views) per second over all
-ranks; Mpix/s, the plain tiled rasterizer on the same inputs, per-stage times
-and the roofline of the dominant kernel are reported beside it.
+orbit cameras at 1264x832. One step renders all 8 views through the whole hot
+path: preprocess -> scan/emit/radix sort/ranges -> render, in one batched
+launch per stage, with the tile shape, warp-block layout and staging batch the
+autotuner picks. ``value`` is frames (views) per second over all ranks; Mpix/s,
+the plain tiled rasterizer on the same inputs, forward + backward, per-stage
+times and the roofline of the dominant kernel (against FP32 and SFU peaks
+measured on the GPU by the library's probe kernels) are reported beside it,
+plus the small (10k), batched (64 views), indoor training and 30M-Gaussian
+configurations.
 
 Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
-launching stream; L2 is flushed (256 MB write) between steps, outside the
-events. Under torchrun each rank renders its own 8 views (replicas: no data
-exchange), and the time is the maximum over ranks.
+launching stream; a step's time is the median over the K steps. L2 is flushed
+(256 MB write) between steps, outside the events. Under torchrun each rank
+renders its own 8 views (replicas: no data exchange), and the time is the
+maximum over ranks.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
-reference arm of this project: there is no other implementation to run).
+reference arm of this project: there is no other implementation to run), one
+full view per step.
 """
 from __future__ import annotations
 
@@ -33,7 +39,6 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "outdoor-500k-sh3-8x1264x832"
 METRIC = "frames/s (Local-GS fwd, 8 views of 1264x832, 500k Gaussians SH3)"
-CROP = (158, 104)          # 1/64 of a 1264x832 view: one oracle sample
 
 
 def parse():
@@ -56,8 +61,11 @@ def parse():
     p.add_argument("--no-scale", action="store_true", help="skip the 30M-Gaussian scale scene")
     p.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint each step")
     p.add_argument("--tight", action="store_true", help="with --profile: tight-box emission")
-    p.add_argument("--scene", default="outdoor", choices=["outdoor", "indoor", "scale"],
-                   help="with --profile: the scene (indoor and scale run through batch.Renderer)")
+    p.add_argument("--scene", default="outdoor", choices=["outdoor", "indoor", "scale", "batched"],
+                   help="with --profile: the scene (the others run through batch.Renderer)")
+    p.add_argument("--block", default="paper",
+                   help="warp block WxH of the Local-GS render with a fixed --tile (paper = full-width strips)")
+    p.add_argument("--no-tiny", action="store_true", help="skip the 10k-Gaussian 256x256 configuration")
     return p.parse_args()
 
 
@@ -105,33 +113,24 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_crops(scene, cams, n_crops, seed=7):
+def oracle_views(scene, cams, n, first=0):
+    """Seconds the FP64 oracle takes to render n full views (preprocess, sort
+    and blend of the whole scene for each), cycling through the cameras."""
     import oracle
-    from paper_2606_16566_gb300 import scenes
-    rng = np.random.default_rng(seed)
-    cam = cams[0]
-    W, H = cam["width"], cam["height"]
     t0 = time.perf_counter()
-    for _ in range(n_crops):
-        x0 = int(rng.integers(0, (W - CROP[0]) // 16)) * 16
-        y0 = int(rng.integers(0, (H - CROP[1]) // 16)) * 16
-        oracle.render(scene, scenes.crop_camera(cam, x0, y0, *CROP))
+    for k in range(n):
+        oracle.render(scene, cams[(first + k) % len(cams)])
     return time.perf_counter() - t0
 
 
-def crop_fraction(cams):
-    return CROP[0] * CROP[1] / (cams[0]["width"] * cams[0]["height"])
-
-
-def cpu_baseline(scene, cams, budget_s=15.0):
+def cpu_baseline(scene, cams, budget_s=15.0, label="500k Gaussians"):
     import oracle
-    t1 = oracle_crops(scene, cams, 1)
-    n = max(1, min(64, int(budget_s / max(t1, 1e-3))))
-    t = oracle_crops(scene, cams, n, seed=11)
-    fps = n * crop_fraction(cams) / t
-    return {"value": fps, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} random {CROP[0]}x{CROP[1]} crops of view 0 (each 1/64 of a frame; full "
-                      f"preprocess+sort of all 500k Gaussians per crop), rate scaled by pixel fraction"}
+    t1 = oracle_views(scene, cams, 1)
+    n = max(1, min(len(cams), int(budget_s / max(t1, 1e-3))))
+    t = oracle_views(scene, cams, n, first=1)
+    W, H = cams[0]["width"], cams[0]["height"]
+    return {"value": n / t, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full {W}x{H} views (FP64 preprocess, sort and blend of all {label} per view)"}
 
 
 def run_reference(args, rank, world):
@@ -140,18 +139,17 @@ def run_reference(args, rank, world):
     from paper_2606_16566_gb300 import scenes
     import oracle
     scene, cams = scenes.outdoor()
-    for _ in range(args.warmup):
-        oracle_crops(scene, cams, 1, seed=3)
-    t = oracle_crops(scene, cams, args.steps, seed=5)
-    fps = args.steps * crop_fraction(cams) / t
+    oracle_views(scene, cams, args.warmup)
+    t = oracle_views(scene, cams, args.steps, first=args.warmup)
+    fps = args.steps / t
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{CROP[0]}x{CROP[1]} crop per step"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "one full 1264x832 view per step"},
         "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"one random {CROP[0]}x{CROP[1]} crop (1/64 frame) of view 0 per step, "
-                                   "rate scaled by pixel fraction"},
+                         "sample": "one full 1264x832 view per step (FP64 preprocess, sort and blend of all "
+                                   "500k Gaussians), views cycling through the 8 cameras"},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -239,6 +237,47 @@ class Pipeline:
         return 1 + (2 + 4) + (1 + 3) + 1 + ((2 + tile_passes) if tile_passes else 0) + 1 + 1
 
 
+def measure_peaks(dev, reps=5):
+    """Throughput of the FP32 FMA pipe (scalar and packed two-wide FMA chains)
+    and of the SFU's ex2 on this GPU, from the library's probe kernels (run
+    outside the timed region), with the SM clock sampled during the probes."""
+    import ctypes
+    import torch
+    from paper_2606_16566_gb300 import _lib as L
+    lib = L.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(sms * 8, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    with Clocks(dev.index) as clk:
+        for name, kind, iters in (("ffma_tflops", L.PROBE_FFMA, 6000), ("ffma2_tflops", L.PROBE_FFMA2, 3000),
+                                  ("ex2_tops", L.PROBE_EX2, 1500)):
+            ts = []
+            ops = ctypes.c_double(0)
+            for _ in range(reps + 2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                L.check(lib.lgs_peak_probe(kind, sms * 8, iters, ctypes.c_void_p(sink.data_ptr()),
+                                           ctypes.byref(ops), stream), "lgs_peak_probe")
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            out[name] = ops.value / (statistics.median(ts[2:]) * 1e-3) / 1e12
+    out["sm_mhz"] = clk.summary()["sm_mhz"]
+    out["how"] = (f"lgs_peak_probe: {sms * 8} CTAs x 256 threads x 8 independent chains; median of {reps} "
+                  "launches, CUDA events")
+    return out
+
+
+def loaded_clock_mhz():
+    """Median SM clock of the GB300s under a power-capped sustained load,
+    when the machine's measured-peaks record is present."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["clocks_under_load"]["sm_mhz_median"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
 def time_steps(pipe, cfg, steps, flush, backward=False):
     import torch
     ns = 4 if backward else 3
@@ -286,9 +325,9 @@ def run_batched(dev, steps):
     sc, cams = scenes.batched()
     g = lgs.to_device(sc, dev)
     del sc
-    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False, tight=True)
+    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False, tight=True, batches=(256,))
     r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True, tight=True,
-                       batch=tune["batch"])
+                       batch=tune["batch"], block=tune["block"])
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -303,13 +342,14 @@ def run_batched(dev, steps):
         if i >= 2:
             ts.append(e0.elapsed_time(e1))
     st = r.check()
-    ms = float(np.mean(ts))
+    ms = float(np.median(ts))
     P = lgs.n_pixels(cams)
     out = {"workload": "batched-3M-sh3-64-uneven-views-fwd+bwd-graph", "emission": "tight",
            "view_groups": len(r.groups),
            "frames_s": len(cams) / (ms * 1e-3),
            "mpix_s": P / 1e6 / (ms * 1e-3), "ms_per_step": ms, "instances_K": int(st[2]),
-           "tile": list(tune["tile"]), "persistent": tune["persistent"], "staging_batch": tune["batch"],
+           "tile": list(tune["tile"]), "warp_block": list(tune["block"]), "persistent": tune["persistent"],
+           "staging_batch": tune["batch"],
            "autotune": tune["timings"],
            "replays": len(ts)}
     del r, g
@@ -329,7 +369,7 @@ def _graph_ms(graph, flush, reps):
         torch.cuda.synchronize()
         if i >= 2:
             ts.append(e0.elapsed_time(e1))
-    return float(np.mean(ts)), len(ts)
+    return float(np.median(ts)), len(ts)
 
 
 def run_indoor(dev, steps):
@@ -410,7 +450,7 @@ def run_scale(dev, steps):
             stage.append([e[k].elapsed_time(e[k + 1]) for k in range(3)])
     st = r.check()
     K = int(st[L.ST_NUM_INSTANCES])
-    sm = np.mean(np.array(stage), 0)
+    sm = np.median(np.array(stage), 0)
     ms_f = float(sm.sum())
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
@@ -432,6 +472,32 @@ def run_scale(dev, steps):
     return out
 
 
+def run_tiny(dev, steps):
+    """The small configuration (10k Gaussians SH0, one 256x256 view, 16x16
+    tiles, forward): every warp-block layout of the 16x16 tile timed, the
+    fastest reported, and the oracle on full frames of the same view beside it."""
+    import torch
+    from paper_2606_16566_gb300 import lgs, scenes
+    from paper_2606_16566_gb300 import _lib as L
+    sc, cams = scenes.tiny()
+    g = lgs.to_device(sc, dev)
+    probe = lgs.render(g, cams, tile=(16, 16), flags=L.FLAG_TIGHT)
+    pipe = Pipeline(g, cams, (16, 16), int(probe["K"] * 1.05) + 1024)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    per = {}
+    for blk in lgs.WARP_BLOCKS[(16, 16)]:
+        cfg = lgs.config((16, 16), "localgs", L.FLAG_TIGHT, 0, blk)
+        for _ in range(3):
+            pipe.step(cfg)
+        per[f"{blk[0]}x{blk[1]}"] = float(np.median(time_steps(pipe, cfg, max(30, steps), flush).sum(1)))
+    best = min(per, key=per.get)
+    ms = per[best]
+    out = {"workload": "tiny-10k-sh0-256x256 (16x16 tiles, tight, fwd)", "frames_s": 1e3 / ms,
+           "mpix_s": 256 * 256 / 1e6 / (ms * 1e-3), "ms_per_step": ms, "block": best, "ms_by_block": per}
+    out["cpu_baseline"] = cpu_baseline(sc, cams, budget_s=3.0, label="10k Gaussians")
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -441,13 +507,15 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
+    block = None if args.block == "paper" else tuple(int(x) for x in args.block.split("x"))
     if args.profile and args.scene != "outdoor":
         from paper_2606_16566_gb300 import batch
         scene, cams = getattr(scenes, args.scene)()
         cams = cams[:args.views]
         g = lgs.to_device(scene, dev)
         del scene
-        r = batch.Renderer(g, cams, tile=tile, mode=args.mode, backward=args.backward, tight=args.tight)
+        r = batch.Renderer(g, cams, tile=tile, mode=args.mode, backward=args.backward, tight=args.tight,
+                           block=block)
         if args.backward:
             r.d_rgb.fill_(1.0 / r.d_rgb.numel())
         for _ in range(args.warmup + args.steps):
@@ -464,7 +532,7 @@ def run_ours(args, rank, world):
         probe = lgs.render(g, cams, tile=tile)
         pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
         del probe
-        cfg = lgs.config(tile, args.mode, L.FLAG_TIGHT if args.tight else 0)
+        cfg = lgs.config(tile, args.mode, L.FLAG_TIGHT if args.tight else 0, 0, block)
         if args.backward:
             pipe.setup_backward()
         for _ in range(args.warmup + args.steps):
@@ -476,23 +544,30 @@ def run_ours(args, rank, world):
     TF = L.FLAG_TIGHT
     tuned = None
     persistent = 0
+    nbat = 0
     if args.tile == "auto":
-        # tile shape and launch of the Local-GS forward from the project's
-        # autotuner (timed graph replays of every candidate, outside the timed region)
+        # tile shape, warp-block layout, staging batch and launch of the
+        # Local-GS forward from the project's autotuner (timed graph replays of
+        # every candidate, outside the timed region)
         from paper_2606_16566_gb300 import batch
         tuned = batch.autotune(g, cams, tight=True, reps=5, use_cache=False)
         tile = tuple(tuned["tile"])
+        block = tuple(tuned["block"])
         persistent = L.FLAG_PERSISTENT if tuned["persistent"] else 0
-    nbat = tuned["batch"] if tuned else 0
+        nbat = tuned["batch"]
+    paper_block = lgs.WARP_BLOCKS[tile][0]
+    block = block or paper_block
     PF = persistent
     # the plain rasterizer runs on the standard 3DGS 16x16 tile, its own best
-    # shape; the Local-GS variants on the tuned one
+    # shape; the Local-GS variants on the tuned tile and block
     tile_p = (16, 16) if args.tile == "auto" else tile
-    variants = {"localgs": lgs.config(tile, "localgs", PF, nbat), "plain": lgs.config(tile_p, "plain"),
-                "localgs_tight": lgs.config(tile, "localgs", TF | PF, nbat),
+    variants = {"localgs": lgs.config(tile, "localgs", PF, nbat, block), "plain": lgs.config(tile_p, "plain"),
+                "localgs_tight": lgs.config(tile, "localgs", TF | PF, nbat, block),
                 "plain_tight": lgs.config(tile_p, "plain", TF), "literal_tight": lgs.config(tile, "literal", TF)}
-    forward_only = {"literal_tight"}       # the paper-literal study variant has no adjoint
-    mode_of = {L.MODE_LOCALGS: "localgs", L.MODE_PLAIN: "plain", L.MODE_LITERAL: "literal"}
+    if tuple(block) != tuple(paper_block):
+        # the same tile in the paper's warp layout (eight full-width strips)
+        variants["localgs_tight_paper_layout"] = lgs.config(tile, "localgs", TF, 0, paper_block)
+    forward_only = {"literal_tight", "localgs_tight_paper_layout"}
 
     # discover K and size the instance buffers once per tile shape (outside the timed region)
     pipes_by_tile = {}
@@ -506,12 +581,13 @@ def run_ours(args, rank, world):
     counts = {}
     for name, cfg in variants.items():
         q = pipe_of[name]
-        q.step(lgs.config((cfg.tile_w, cfg.tile_h), mode_of[cfg.mode], cfg.flags | L.FLAG_COUNT, cfg.batch))
+        q.step(lgs.with_flags(cfg, cfg.flags | L.FLAG_COUNT))
         st = lgs.read_status(q.status)
         if st[L.ST_CODE] != 0:
             raise L.LgsError(int(st[L.ST_CODE]), f"device status in {name}")
         counts[name] = {"pairs": int(st[L.ST_PAIRS]), "K": int(st[L.ST_NUM_INSTANCES])}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks = measure_peaks(dev)
 
     for q in pipes_by_tile.values():
         q.setup_backward()
@@ -537,8 +613,9 @@ def run_ours(args, rank, world):
         st = lgs.read_status(q.status)
         if st[L.ST_CODE] != 0:
             raise L.LgsError(int(st[L.ST_CODE]), "device status after the timed steps")
-    ms = {n: float(fwd[n].sum(1).mean()) for n in variants}
-    ms_b = {n: float(fb[n].sum(1).mean()) for n in fb}
+    # step time: the median of the timed steps (each the sum of its stages)
+    ms = {n: float(np.median(fwd[n].sum(1))) for n in variants}
+    ms_b = {n: float(np.median(fb[n].sum(1))) for n in fb}
     names, names_b = list(ms), list(ms_b)
     vals = reduce_max_over_ranks([ms[n] for n in names] + [ms_b[n] for n in names_b], world, dev)
     ms = dict(zip(names, vals[:len(names)]))
@@ -549,23 +626,26 @@ def run_ours(args, rank, world):
     head = min(("localgs", "localgs_tight"), key=lambda n: ms[n])
     ms_l = ms[head]
     fps = world * views / (ms_l * 1e-3)
-    stage_ms = fwd[head].mean(0)
-    render_ms = float(stage_ms[2])
-    sm_max = 2070.0
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 TFLOP/s at max SM clock
-    flops = counts[head]["pairs"] * 19.0
-    achieved = flops / (render_ms * 1e-3) / 1e12
+    stage_ms = np.median(fwd[head], 0)
+    # the render kernel's average launch time over the timed steps (CUDA events
+    # around its one launch per step, on the launching stream)
+    render_ms = float(fwd[head][:, 2].mean())
+    pairs = counts[head]["pairs"]
+    achieved = pairs * 19.0 / (render_ms * 1e-3) / 1e12
+    peak = max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
+    sfu_rate = pairs / (render_ms * 1e-3) / 1e12
     cfg_l = variants[head]
+    loaded = loaded_clock_mhz()
+    probe_mhz = peaks["sm_mhz"] or 2070.0
 
     def summary(name):
-        f = fwd[name].mean(0)
+        f = np.median(fwd[name], 0)
         out = {"frames_s": world * views / (ms[name] * 1e-3), "mpix_s": world * P / 1e6 / (ms[name] * 1e-3),
                "ms_per_step": ms[name],
                "stage_ms": {"preprocess": float(f[0]), "sort": float(f[1]), "render": float(f[2])},
                "instances_K": counts[name]["K"], "pairs": counts[name]["pairs"]}
         if name in fb:
-            b = fb[name].mean(0)
+            b = np.median(fb[name], 0)
             out["fwd_bwd"] = {"frames_s": world * views / (ms_b[name] * 1e-3),
                               "mpix_s": world * P / 1e6 / (ms_b[name] * 1e-3), "ms_per_step": ms_b[name],
                               "backward_ms": float(b[3])}
@@ -630,6 +710,7 @@ def run_ours(args, rank, world):
                "schedule": "2 buffer sets, upload / render / download of consecutive steps on 3 streams"}
         del pipes[1], gs[1]
 
+    tiny = None if args.no_tiny else run_tiny(dev, args.steps)
     batched, n_batched = (None, 0)
     if not args.no_batched:
         batched, n_batched = run_batched(dev, args.steps)
@@ -639,39 +720,59 @@ def run_ours(args, rank, world):
         return
     emission = "tight" if head.endswith("tight") else "rect"
     plain_same = "plain_tight" if emission == "tight" else "plain"
+    s_head, s_plain = summary(head), summary(plain_same)
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "views_per_step": views, "gaussians": pipe.n,
-                   "tile": f"{tile[0]}x{tile[1]}", "persistent": bool(persistent),
-                   "staging_batch": nbat or 256,
+                   "tile": f"{tile[0]}x{tile[1]}", "warp_block": f"{block[0]}x{block[1]}",
+                   "persistent": bool(persistent), "staging_batch": nbat or 256,
                    "tile_choice": "autotuned" if tuned else "fixed",
                    "plain_tile": f"{tile_p[0]}x{tile_p[1]}",
                    "emission": emission, "instances_K": counts[head]["K"],
+                   "step_time": f"median of {args.steps} timed steps",
                    "l2": "flushed between steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
-        "mpix_s": world * P / 1e6 / (ms_l * 1e-3),
-        "stage_ms": {"preprocess": float(stage_ms[0]), "sort": float(stage_ms[1]), "render": render_ms},
-        "fwd_bwd": summary(head)["fwd_bwd"],
-        "plain": summary(plain_same),
-        "render_speedup_vs_plain": float(fwd[plain_same].mean(0)[2]) / render_ms,
         "variants": {n: summary(n) for n in variants},
         "upstream_grad": "fixed +-1/numel dL/drgb (L1-loss shaped), 3D grads zeroed each step",
         "autotune": tuned["timings"] if tuned else None,
-        "roofline": {"bound": "alu", "kernel": "render_localgs" + ("_persistent" if persistent else ""), "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(f"render_localgs{'_persistent' if persistent else ''}"
-                                                 f"_{tile[0]}x{tile[1]}_{emission}"),
-                     "work": f"{counts[head]['pairs']} pixel-Gaussian pairs x 19 FP32 flops",
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (of nominal max clock)"},
+        "peaks": peaks,
+        "batched": batched,
+        "indoor": indoor,
+        "scale": scale,
+        "tiny": tiny,
         "gpu_launches": sum(pipe_of[n].launches() * args.steps for n in variants)
                         + sum((pipe_of[n].launches() + 2) * n_bw for n in fb),
         "clocks": clk.summary(),
         "e2e": e2e,
-        "batched": batched,
-        "indoor": indoor,
-        "scale": scale,
+        "roofline": {"bound": "alu", "kernel": "render_localgs" + ("_persistent" if persistent else ""),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(f"render_localgs{'_persistent' if persistent else ''}"
+                                                 f"_{tile[0]}x{tile[1]}_{block[0]}x{block[1]}_{emission}"),
+                     "work": f"{pairs} pixel-Gaussian pairs x 19 FP32 flops",
+                     "peak_basis": f"measured: FP32 FMA-chain probe (scalar {peaks['ffma_tflops']:.1f}, "
+                                   f"packed {peaks['ffma2_tflops']:.1f} TFLOP/s) at {probe_mhz:.0f} MHz",
+                     "peak_at_loaded_clock": peak * loaded / probe_mhz if loaded else None,
+                     "loaded_clock_mhz": loaded,
+                     "sfu": {"achieved": sfu_rate, "peak": peaks["ex2_tops"], "unit": "T ex2/s",
+                             "frac": sfu_rate / peaks["ex2_tops"]}},
+        "comparison": {
+            "localgs_fwd_frames_s": fps, "plain_fwd_frames_s": s_plain["frames_s"],
+            "fwd_ratio": s_plain["ms_per_step"] / ms_l,
+            "localgs_fwd_bwd_frames_s": s_head["fwd_bwd"]["frames_s"],
+            "plain_fwd_bwd_frames_s": s_plain["fwd_bwd"]["frames_s"],
+            "fwd_bwd_ratio": s_plain["fwd_bwd"]["ms_per_step"] / s_head["fwd_bwd"]["ms_per_step"],
+            "render_kernel_ratio": float(np.median(fwd[plain_same][:, 2])) / float(np.median(fwd[head][:, 2])),
+            "localgs_mpix_s": s_head["mpix_s"], "plain_mpix_s": s_plain["mpix_s"],
+            "stage_ms": s_head["stage_ms"], "backward_ms": s_head["fwd_bwd"]["backward_ms"],
+            "emission": emission, "tile": f"{tile[0]}x{tile[1]}", "warp_block": f"{block[0]}x{block[1]}",
+            "plain_tile": f"{tile_p[0]}x{tile_p[1]}",
+            "batched_fwd_bwd_frames_s": batched["frames_s"] if batched else None,
+            "indoor_steps_s": indoor["steps_s"] if indoor else None,
+            "scale_fwd_frames_s": scale["frames_s"] if scale else None,
+            "scale_fwd_bwd_frames_s": scale["fwd_bwd"]["frames_s"] if scale else None,
+            "tiny_fwd_frames_s": tiny["frames_s"] if tiny else None},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cams)

@@ -136,16 +136,26 @@ typedef struct {
  * points ignore the flag (they follow the lists they are given). */
 #define LGS_FLAG_TIGHT 4
 
-/* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}; 8 warps per tile, each a
- * tile_w x tile_h/8 strip), render mode and flags. batch = Gaussians the
- * Local-GS render (LGS_MODE_LOCALGS) stages in shared memory per round: 0
- * (= 256), 64, 128 or 256, else LGS_ERR_UNSUPPORTED; the results do not depend
- * on it. The other modes and the adjoint stage 256. */
+/* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}), render mode and flags.
+ * batch = Gaussians the Local-GS render (LGS_MODE_LOCALGS) stages in shared
+ * memory per round: 0 (= 256), 64, 128 or 256, else LGS_ERR_UNSUPPORTED; the
+ * results do not depend on it. The other modes and the adjoint stage 256.
+ * warp_w x warp_h = the pixel block one warp of the Local-GS render owns, with
+ * its own bit of the culling mask (Sec. III-C3; the paper's layout, and the
+ * default 0 x 0, is eight full-width strips of tile_h/8 rows). Blocks of 32
+ * pixels run one pixel per lane, blocks of 64 pixels two pixels per lane with
+ * packed two-wide FP32 arithmetic (4 warps per tile). Supported: 16x16 tiles
+ * with 16x2, 8x4 (2 x 4 blocks: the mask also culls by column half), 16x4 or
+ * 8x8 blocks; 8x32 tiles with 8x4 or 8x8; 32x8 tiles with 32x1 or 8x8. Other
+ * blocks, or a non-default block with LGS_MODE_PLAIN/LITERAL/GLOBAL, return
+ * LGS_ERR_UNSUPPORTED. Outputs do not depend on the block layout (bit for bit);
+ * only the work the mask saves does. Other entry points ignore the two fields. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t mode;
     int32_t batch;
     int32_t flags;
+    int32_t warp_w, warp_h;
 } lgs_config;
 
 /* Per-(view, Gaussian) preprocess outputs, M = n_views * N entries each,

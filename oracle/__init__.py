@@ -76,6 +76,11 @@ def lib():
         L.orc_localgs_pairs.restype = ctypes.c_int64
         L.orc_localgs_pairs.argtypes = [ctypes.c_int] * 5 + [_u32p, _u32p, ctypes.c_int64,
                                                              _dp, _dp, _dp, _u32p]
+        L.orc_localgs_pairs_blocks.restype = ctypes.c_int64
+        L.orc_localgs_pairs_blocks.argtypes = [ctypes.c_int] * 6 + [_u32p, _u32p, ctypes.c_int64,
+                                                                    _dp, _dp, _dp, _u32p]
+        L.orc_block_mask.restype = ctypes.c_uint32
+        L.orc_block_mask.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int] * 6
         if hasattr(L, "orc_backward"):
             _bind_backward(L)
         _LIB = L
@@ -238,15 +243,22 @@ def tight_rows(a, b, c, o, mux, muy, X0, ry0, ry1, tile_w=16, tile_h=16, band_ta
     return lo.value, hi.value, int(k), bool(gd.value)
 
 
-def localgs_pairs(res, cam, tile_w=16, tile_h=16, n_warps=8):
-    """Pixel-Gaussian pairs of the Local-GS schedule (warp mask + warp exit)."""
+def block_mask(a, b, c, o, mux, muy, X0, Y0, tile_w=16, tile_h=16, block_w=16, block_h=2):
+    """Mask of (tile_w/block_w) x (tile_h/block_h) warp blocks, bit by*nbx + bx."""
+    return int(lib().orc_block_mask(a, b, c, o, mux, muy, X0, Y0, tile_w, tile_h, block_w, block_h))
+
+
+def localgs_pairs(res, cam, tile_w=16, tile_h=16, n_warps=8, block=None):
+    """Pixel-Gaussian pairs of the Local-GS schedule (warp mask + warp exit);
+    block = (block_w, block_h) of one warp, None = n_warps full-width strips."""
     pre = res["pre"]
     W, H = cam["width"], cam["height"]
+    bw, bh = (tile_w, tile_h // n_warps) if block is None else block
     v = np.ascontiguousarray(res["vals"], np.uint32) if len(res["vals"]) else np.zeros(1, np.uint32)
-    return int(lib().orc_localgs_pairs(W, H, tile_w, tile_h, n_warps, _p(v, _u32p),
-                                       _p(res["ranges"], _u32p), 0, _p(pre["uv"], _dp),
-                                       _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
-                                       _p(np.ascontiguousarray(res["stop_pos"]), _u32p)))
+    return int(lib().orc_localgs_pairs_blocks(W, H, tile_w, tile_h, bw, bh, _p(v, _u32p),
+                                              _p(res["ranges"], _u32p), 0, _p(pre["uv"], _dp),
+                                              _p(pre["conic"], _dp), _p(pre["opacity"], _dp),
+                                              _p(np.ascontiguousarray(res["stop_pos"]), _u32p)))
 
 
 def backward(scene, cam, dL_drgb, dL_dT=None, tile_w=16, tile_h=16, exact=False):
@@ -298,7 +310,8 @@ def ewa(cam, t, Sig):
     return out
 
 
-__all__ = ["render", "backward", "preprocess", "sort", "blend", "blend_literal", "hoist", "warp_mask", "tight_rows",
+__all__ = ["render", "backward", "preprocess", "sort", "blend", "blend_literal", "hoist", "warp_mask",
+           "block_mask", "tight_rows",
            "localgs_pairs",
            "sh_basis", "quat_to_rot", "cov3d", "ewa", "num_threads", "cam_array",
            "DEFAULT_GUARD"]

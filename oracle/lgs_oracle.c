@@ -35,6 +35,11 @@
  *                    alpha inside its warp's box and no pixel stops; T stays
  *                    the product of (1 - alpha); brute force per strip)
  *   orc_warp_mask    pinned (brute-force sampling of the ellipse)
+ *   orc_block_mask   pinned (brute-force row intersection per block column;
+ *                    superset of every pixel with alpha >= 1/255)
+ *   orc_localgs_pairs / orc_localgs_pairs_blocks
+ *                    pinned (closed-form counts: one Gaussian without a stop,
+ *                    a stack whose every pixel stops at one position)
  *   orc_tight_rows   pinned (brute-force alpha over every pixel of the rect:
  *                    no dropped tile holds a pixel with alpha >= 1/255; every
  *                    kept tile holds a pixel inside the widened ellipse)
@@ -588,34 +593,54 @@ uint32_t orc_warp_mask(double a, double b, double c, double o, double mux, doubl
     return ((1u << (we - ws + 1)) - 1u) << ws;
 }
 
-/* Work of the Local-GS schedule in pixel-Gaussian pairs: for every tile and
- * every warp strip, the Gaussians of the tile list whose mask bit for the
- * strip is set, counted up to and including the first one after which every
- * pixel of the strip has stopped (or the end of the list); times the pixels
- * of the strip (the lanes of a warp). n_contrib/stop positions come from the
- * blend above: a pixel has stopped once the list position passes its stop
- * position. stop_pos[pix] = list position (1-based) of the Gaussian that
- * triggered the stop, or 0 when the pixel never stopped. */
-int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
-                          const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
-                          const double* uv, const double* conic, const double* opac,
-                          const uint32_t* stop_pos) {
+/* Block mask: the tile cut into (tile_w/block_w) x (tile_h/block_h) blocks,
+ * block (bx, by) owning bit by * (tile_w/block_w) + bx. Each block column is
+ * the pixel-column strip of orc_warp_mask above (its own tight box over its
+ * own x-range), split into strips of block_h rows; with block_w = tile_w this
+ * is orc_warp_mask with tile_h/block_h strips. */
+uint32_t orc_block_mask(double a, double b, double c, double o, double mux, double muy,
+                        int X0, int Y0, int tile_w, int tile_h, int block_w, int block_h) {
+    int nbx = tile_w / block_w, nby = tile_h / block_h;
+    uint32_t m = 0u;
+    for (int bx = 0; bx < nbx; ++bx) {
+        uint32_t col = orc_warp_mask(a, b, c, o, mux, muy, X0 + bx * block_w, Y0, block_w, tile_h, nby);
+        for (int by = 0; by < nby; ++by)
+            if (col & (1u << by)) m |= 1u << (by * nbx + bx);
+    }
+    return m;
+}
+
+/* Work of the Local-GS schedule in pixel-Gaussian pairs, for a warp layout of
+ * block_w x block_h pixel blocks (one warp each): for every tile and block,
+ * the Gaussians of the tile list whose mask bit for the block is set, counted
+ * up to and including the first one after which every pixel of the block has
+ * stopped (or the end of the list); times the pixels of the block (the
+ * evaluations its warp issues). n_contrib/stop positions come from the blend
+ * above: a pixel has stopped once the list position passes its stop position.
+ * stop_pos[pix] = list position (1-based) of the Gaussian that triggered the
+ * stop, or 0 when the pixel never stopped; pixels outside the image count as
+ * stopped. */
+int64_t orc_localgs_pairs_blocks(int W, int H, int tile_w, int tile_h, int block_w, int block_h,
+                                 const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
+                                 const double* uv, const double* conic, const double* opac,
+                                 const uint32_t* stop_pos) {
     int gx = (W + tile_w - 1) / tile_w, gy = (H + tile_h - 1) / tile_h;
-    int rows = tile_h / n_warps;
+    int nbx = tile_w / block_w, nby = tile_h / block_h;
     int64_t total = 0;
     for (int ty = 0; ty < gy; ++ty)
         for (int tx = 0; tx < gx; ++tx) {
             int64_t tile = tile_offset + (int64_t)ty * gx + tx;
             uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
             int X0 = tx * tile_w, Y0 = ty * tile_h;
-            for (int w = 0; w < n_warps; ++w) {
-                /* stop position of the warp = max over its pixels (0 = never) */
+            for (int w = 0; w < nbx * nby; ++w) {
+                int bx = w % nbx, by = w / nbx;
+                /* stop position of the block = max over its pixels (0 = never) */
                 uint32_t wstop = 0;
                 int never = 0;
-                for (int r = 0; r < rows; ++r)
-                    for (int cc = 0; cc < tile_w; ++cc) {
-                        int px = X0 + cc, py = Y0 + w * rows + r;
-                        if (px >= W || py >= H) continue;      /* out-of-image lanes are done */
+                for (int r = 0; r < block_h; ++r)
+                    for (int cc = 0; cc < block_w; ++cc) {
+                        int px = X0 + bx * block_w + cc, py = Y0 + by * block_h + r;
+                        if (px >= W || py >= H) continue;
                         uint32_t sp = stop_pos[(int64_t)py * W + px];
                         if (sp == 0) never = 1;
                         else if (sp > wstop) wstop = sp;
@@ -624,14 +649,23 @@ int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
                     uint32_t pos = k - s + 1;
                     if (!never && pos > wstop) break;
                     uint32_t id = vals[k];
-                    uint32_t m = orc_warp_mask(conic[3 * id], conic[3 * id + 1], conic[3 * id + 2],
-                                               opac[id], uv[2 * id], uv[2 * id + 1], X0, Y0,
-                                               tile_w, tile_h, n_warps);
-                    if (m & (1u << w)) total += (int64_t)rows * tile_w;
+                    uint32_t m = orc_block_mask(conic[3 * id], conic[3 * id + 1], conic[3 * id + 2],
+                                                opac[id], uv[2 * id], uv[2 * id + 1], X0, Y0,
+                                                tile_w, tile_h, block_w, block_h);
+                    if (m & (1u << w)) total += (int64_t)block_w * block_h;
                 }
             }
         }
     return total;
+}
+
+/* The paper's layout: n_warps full-width strips of tile_h/n_warps rows. */
+int64_t orc_localgs_pairs(int W, int H, int tile_w, int tile_h, int n_warps,
+                          const uint32_t* vals, const uint32_t* ranges, int64_t tile_offset,
+                          const double* uv, const double* conic, const double* opac,
+                          const uint32_t* stop_pos) {
+    return orc_localgs_pairs_blocks(W, H, tile_w, tile_h, tile_w, tile_h / n_warps, vals, ranges,
+                                    tile_offset, uv, conic, opac, stop_pos);
 }
 
 /* ------------------------------------------------------------------ */

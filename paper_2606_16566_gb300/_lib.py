@@ -55,7 +55,8 @@ class lgs_gaussians(ctypes.Structure):
 
 class lgs_config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("batch", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("batch", ctypes.c_int32), ("flags", ctypes.c_int32), ("warp_w", ctypes.c_int32),
+                ("warp_h", ctypes.c_int32)]
 
 
 class lgs_pre_out(ctypes.Structure):

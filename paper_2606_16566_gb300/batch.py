@@ -10,9 +10,10 @@ Cameras and the instance capacity are baked into a captured graph; scene
 tensors and the upstream gradient are read in place, so they may change
 between replays.
 
-``autotune`` times the candidate tile shapes (16x16, 8x32, 32x8: the warp
-strip of a 256-thread tile is 16x2, 8x4 or 32x1 pixels), with and without the
-persistent render launch and with staging batches of 256 or 128 Gaussians, on
+``autotune`` times the candidate tile shapes (16x16, 8x32, 32x8) with every
+warp-block layout of the Local-GS render for that shape (the paper's
+full-width strips, 2D blocks, two-pixels-per-lane blocks) and staging batches
+of 256 or 128 Gaussians, then the persistent launch of the best of them, on
 the actual workload, and caches the fastest per (Gaussian-count bucket,
 pixel-count bucket, view count, mode, emission).
 """
@@ -61,10 +62,11 @@ class Renderer:
     output."""
 
     def __init__(self, g, cams, tile=(16, 16), mode="localgs", persistent=False, capacity=None,
-                 headroom=1.10, backward=False, tight=False, max_group_tiles=MAX_GROUP_TILES, batch=0):
+                 headroom=1.10, backward=False, tight=False, max_group_tiles=MAX_GROUP_TILES, batch=0,
+                 block=None):
         self.g, self.cams, self.tile, self.mode = g, cams, tuple(tile), mode
         flags = (L.FLAG_PERSISTENT if persistent else 0) | (L.FLAG_TIGHT if tight else 0)
-        self.cfg = lgs.config(tile, mode, flags, batch)
+        self.cfg = lgs.config(tile, mode, flags, batch, block)
         self.carr = lgs.cameras(cams)
         dev = g["means"].device
         self.n = g["means"].shape[0]
@@ -138,7 +140,7 @@ class Renderer:
     def count_pairs(self):
         """(pixel-Gaussian pairs, warp candidates) of the Local-GS schedule over
         all groups (an extra render with LGS_FLAG_COUNT after a forward)."""
-        cfg = lgs.config(self.tile, self.mode, self.cfg.flags | L.FLAG_COUNT, self.cfg.batch)
+        cfg = lgs.with_flags(self.cfg, self.cfg.flags | L.FLAG_COUNT)
         for q in self.parts:
             q["status"][L.ST_PAIRS] = 0
             q["status"][L.ST_CANDIDATES] = 0
@@ -223,10 +225,11 @@ def default_cache_path():
 
 
 def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persistent=(False, True),
-             reps=10, cache_path=None, use_cache=True, tight=False, batches=(256, 128)):
-    """Times every (tile shape, persistent launch, staging batch) candidate with
-    graph replays and returns {"tile": (w, h), "persistent": bool, "batch": b,
-    "ms": t, "timings": [...]}."""
+             reps=10, cache_path=None, use_cache=True, tight=False, batches=(256, 128), blocks=True):
+    """Times every (tile shape, warp block, staging batch) candidate with graph
+    replays, then the persistent launch of the fastest, and returns {"tile":
+    (w, h), "block": (bw, bh), "persistent": bool, "batch": b, "ms": t,
+    "timings": [...]}. blocks=False keeps the paper's full-width strips."""
     cache_path = cache_path or default_cache_path()
     key = _bucket_key(g["means"].shape[0], cams, mode, backward, tight)
     cache = {}
@@ -235,41 +238,51 @@ def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persis
             cache = json.load(open(cache_path))
         except (OSError, ValueError):
             cache = {}
-        if key in cache:
+        if key in cache and "block" in cache[key]:
             c = cache[key]
-            return {"tile": tuple(c["tile"]), "persistent": c["persistent"], "batch": c.get("batch", 256),
-                    "ms": c["ms"], "timings": c.get("timings", []), "cached": True}
+            return {"tile": tuple(c["tile"]), "block": tuple(c["block"]), "persistent": c["persistent"],
+                    "batch": c.get("batch", 256), "ms": c["ms"], "timings": c.get("timings", []),
+                    "cached": True}
     timings = []
+    caps = {}
+
+    def run(tile, block, pers, nb):
+        r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward, tight=tight,
+                     batch=nb, block=block, capacity=caps.get(tuple(tile)))
+        caps.setdefault(tuple(tile), [p["cap"] for p in r.parts] if len(r.parts) > 1 else r.parts[0]["cap"])
+        if backward:
+            r.d_rgb.fill_(1.0 / r.d_rgb.numel())
+        r.capture()
+        ts = []
+        for _ in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r.graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        r.check()
+        timings.append({"tile": list(tile), "block": list(block), "persistent": pers, "batch": nb,
+                        "ms": float(np.median(ts[2:]))})
+        del r
+        torch.cuda.empty_cache()
+
     for tile in shapes:
-        for pers in persistent:
-            if pers and mode != "localgs":
-                continue
+        layouts = lgs.WARP_BLOCKS[tuple(tile)] if (blocks and mode == "localgs") else \
+            lgs.WARP_BLOCKS[tuple(tile)][:1]
+        for block in layouts:
             for nb in (batches if mode == "localgs" else (256,)):
-                r = Renderer(g, cams, tile=tile, mode=mode, persistent=pers, backward=backward, tight=tight,
-                             batch=nb)
-                if backward:
-                    r.d_rgb.fill_(1.0 / r.d_rgb.numel())
-                r.capture()
-                ts = []
-                for _ in range(reps + 2):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record()
-                    r.graph.replay()
-                    e1.record()
-                    torch.cuda.synchronize()
-                    ts.append(e0.elapsed_time(e1))
-                r.check()
-                timings.append({"tile": list(tile), "persistent": pers, "batch": nb,
-                                "ms": float(np.median(ts[2:]))})
-                del r
-                torch.cuda.empty_cache()
+                run(tile, block, False, nb)
+    if mode == "localgs" and True in persistent:
+        best = min(timings, key=lambda t: t["ms"])
+        run(tuple(best["tile"]), tuple(best["block"]), True, best["batch"])
     best = min(timings, key=lambda t: t["ms"])
-    cache[key] = {"tile": best["tile"], "persistent": best["persistent"], "batch": best["batch"],
-                  "ms": best["ms"], "timings": timings}
+    cache[key] = {"tile": best["tile"], "block": best["block"], "persistent": best["persistent"],
+                  "batch": best["batch"], "ms": best["ms"], "timings": timings}
     try:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1)
     except OSError:
         pass
-    return {"tile": tuple(best["tile"]), "persistent": best["persistent"], "batch": best["batch"],
-            "ms": best["ms"], "timings": timings, "cached": False}
+    return {"tile": tuple(best["tile"]), "block": tuple(best["block"]), "persistent": best["persistent"],
+            "batch": best["batch"], "ms": best["ms"], "timings": timings, "cached": False}

@@ -239,22 +239,46 @@ __device__ __forceinline__ int tight_tile_rows(const TightBox& t, int X0, int tw
     return h >= l ? h - l + 1 : 0;
 }
 
-// Warp-strip mask of one Gaussian for one tile (Sec. III-C2/C3): the rows of
-// the tile that the conservative tight box of the tile's column strip reaches
-// (column_rows), grouped by warp strip. Every pixel whose FP32 alpha clears
-// 1/255 lies in a set strip.
+// Warp-block mask of one Gaussian for one tile (Sec. III-C2/C3, with the
+// paper's 8-bit mask of full-width row strips generalised to 2D blocks): the
+// tile is cut into (TW/WX) x (TH/WY) blocks of WX x WY pixels, block
+// (bx, by) owning bit by * (TW/WX) + bx. For every block column the
+// conservative tight box is evaluated over that column's pixel range
+// (column_rows), and the bits of the blocks whose rows it reaches are set.
+// Every pixel whose FP32 alpha clears 1/255 lies in a set block. With WX = TW
+// the blocks are the paper's full-width row strips.
+template <int TW, int TH, int WX, int WY>
+__device__ __forceinline__ uint32_t block_mask(float a, float b, float c, float o, float mux,
+                                               float muy, int X0, int Y0) {
+    constexpr int NBX = TW / WX, NBY = TH / WY;
+    static_assert(TW % WX == 0 && TH % WY == 0 && NBX * NBY <= 8, "at most 8 blocks per tile");
+    const TightBox tb = tight_box(a, b, c, o, mux, muy);
+    if (tb.kind == 0) return 0u;
+    if (tb.kind == 2) return (1u << (NBX * NBY)) - 1u;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int bx = 0; bx < NBX; ++bx) {
+        int P = 0, Q = 0;
+        if (column_rows(tb, X0 + bx * WX, WX, &P, &Q) != 1) continue;
+        const int ys = max(Y0, P), ye = min(Y0 + TH - 1, Q);
+        if (ys > ye) continue;
+        const int bs = (ys - Y0) / WY, be = (ye - Y0) / WY;
+        if (NBX == 1) {
+            m |= ((1u << (be - bs + 1)) - 1u) << bs;
+        } else {
+#pragma unroll
+            for (int by = 0; by < NBY; ++by)
+                if (by >= bs && by <= be) m |= 1u << (by * NBX + bx);
+        }
+    }
+    return m;
+}
+
+// The 8-strip mask of the paper's layout: eight full-width strips of TH/8 rows.
 template <int TW, int TH>
 __device__ __forceinline__ uint32_t warp_mask(float a, float b, float c, float o, float mux,
                                               float muy, int X0, int Y0) {
-    constexpr int ROWS = TH / 8;
-    int P = 0, Q = 0;
-    const int r = column_rows(tight_box(a, b, c, o, mux, muy), X0, TW, &P, &Q);
-    if (r == 0) return 0u;
-    if (r == 2) return 0xffu;
-    const int ys = max(Y0, P), ye = min(Y0 + TH - 1, Q);
-    if (ys > ye) return 0u;
-    const int ws = (ys - Y0) / ROWS, we = (ye - Y0) / ROWS;
-    return ((1u << (we - ws + 1)) - 1u) << ws;
+    return block_mask<TW, TH, TW, TH / 8>(a, b, c, o, mux, muy, X0, Y0);
 }
 
 }  // namespace lgs

@@ -15,6 +15,20 @@ inline bool tile_shape_ok(int tw, int th) {
     return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8);
 }
 
+// The Local-GS render's warp block (see lgs_config): 0 x 0 selects the
+// paper's full-width strips; returns false for an unsupported block.
+inline bool warp_block(const lgs_config* cfg, int* wx, int* wy) {
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    int x = cfg->warp_w, y = cfg->warp_h;
+    if (x == 0 && y == 0) { x = tw; y = th / 8; }
+    const bool ok = (x == tw && y == th / 8) || (x == 8 && y == 8) ||
+                    (tw == 16 && th == 16 && ((x == 8 && y == 4) || (x == 16 && y == 4)));
+    if (!ok) return false;
+    *wx = x;
+    *wy = y;
+    return true;
+}
+
 // Builds the per-view constant table. Tile ids and pixel offsets are global
 // across the batch (views concatenated in order).
 inline lgs_status make_views(const lgs_camera* cams, int32_t n_views, const lgs_config* cfg,

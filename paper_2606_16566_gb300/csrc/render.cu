@@ -100,13 +100,53 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 }
 
 // ------------------------------------------------------------------ Local-GS
+// Warp layout of a Local-GS tile: NW = (TW/WX) * (TH/WY) warps, warp w owning
+// the WX x WY pixel block (w % (TW/WX), w / (TW/WX)) and bit w of the block
+// mask. Lane l evaluates pixel (l % WX, l / WX) of its block; with 64-pixel
+// blocks (PPL = 2 pixels per lane) also the pixel WY/2 rows below, and the
+// per-pixel FP32 arithmetic of the pair runs as packed two-wide instructions
+// (fma.rn.f32x2 / mul.rn.f32x2), one issue slot for both pixels. The paper's
+// layout is WX = TW, WY = TH/8 (eight full-width strips, one pixel per lane).
+template <int TW, int TH, int WX, int WY>
+struct Layout {
+    static constexpr int NBX = TW / WX, NBY = TH / WY, NW = NBX * NBY, NT = 32 * NW;
+    static constexpr int PPL = WX * WY / 32;
+    static_assert(TW % WX == 0 && TH % WY == 0, "blocks tile the tile");
+    static_assert(PPL == 1 || PPL == 2, "one or two pixels per lane");
+    static_assert(NW == 4 || NW == 8, "4 or 8 warps per tile");
+    static_assert(32 % WX == 0 || WX == 32, "a warp row is whole lanes");
+};
+
+// P pixels' worth of one float, with the packed FP32 operations on two.
+template <int P> struct Px;
+template <> struct Px<1> {
+    float v;
+    __device__ __forceinline__ float& operator[](int) { return v; }
+    __device__ __forceinline__ float operator[](int) const { return v; }
+};
+template <> struct Px<2> {
+    float2 v;
+    __device__ __forceinline__ float& operator[](int k) { return k ? v.y : v.x; }
+    __device__ __forceinline__ float operator[](int k) const { return k ? v.y : v.x; }
+};
+__device__ __forceinline__ Px<1> pfma(Px<1> a, Px<1> b, Px<1> c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Px<2> pfma(Px<2> a, Px<2> b, Px<2> c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Px<1> pmul(Px<1> a, Px<1> b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<2> pmul(Px<2> a, Px<2> b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<1> padd(Px<1> a, Px<1> b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<2> padd(Px<2> a, Px<2> b) { return {__fadd2_rn(a.v, b.v)}; }
+template <int P> __device__ __forceinline__ Px<P> bcast(float s);
+template <> __device__ __forceinline__ Px<1> bcast<1>(float s) { return {s}; }
+template <> __device__ __forceinline__ Px<2> bcast<2>(float s) { return {make_float2(s, s)}; }
+
+template <int NB>
 struct LocalSmem {
-    float4 raw[2][3][BATCH];  // double-buffered cp.async landing zone: xy, conic, rgb records
-    float4 sV[BATCH];         // (A, B, C, F), log2 domain
-    float2 sDE[BATCH];        // (D, E)
-    float4 sC[BATCH];         // (r, g, b, -)
-    uint8_t sM[BATCH];        // warp-strip mask
-    uint8_t sL[8][BATCH];     // per warp: batch indices of its set mask bits, in order
+    float4 raw[2][3][NB];  // double-buffered cp.async landing zone: xy, conic, rgb records
+    float4 sV[NB];         // (A, B, C, F), log2 domain
+    float2 sDE[NB];        // (D, E)
+    float4 sC[NB];         // (-r, -g, -b, -): colour negated, see the blend
+    uint8_t sM[NB];        // warp-block mask
+    uint8_t sL[8][NB];     // per warp: batch indices of its set mask bits, in order
 };
 
 // 16-byte asynchronous global -> shared copy (cp.async, cached in L2 only:
@@ -125,82 +165,120 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //  VAR_LITERAL:  Alg. 1 right column read literally (Sec. III-D): no per-pixel
 //                1/255 test (the warp mask is the only culling), w = alpha T,
 //                C += f w, T -= w, and the warp leaves its list once every
-//                lane has T < 1e-4 (checked before each Gaussian);
+//                pixel it owns has T < 1e-4 (checked before each Gaussian);
 //  VAR_GLOBAL:   the contract evaluated with the hoist in global pixel
 //                coordinates (origin at pixel (0, 0)): the "w/o local coord"
 //                configuration of Sec. III-B4 / Table V, kept for the FP32
 //                precision study.
 constexpr int VAR_CONTRACT = 0, VAR_LITERAL = 1, VAR_GLOBAL = 2;
+constexpr float INF_F = __builtin_huge_valf();
 
-template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT, int NB = BATCH>
+template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
 __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t tile,
-                                             LocalSmem& S) {
+                                             LocalSmem<NB>& S) {
+    using Lay = Layout<TW, TH, WX, WY>;
+    constexpr int PPL = Lay::PPL, NT = Lay::NT;
     static_assert(NB == 64 || NB == 128 || NB == 256, "staging batch of 64, 128 or 256 Gaussians");
-    float4* sV = S.sV;
-    float2* sDE = S.sDE;
-    float4* sC = S.sC;
-    uint8_t* sM = S.sM;
-    TileCtx t = tile_ctx<TW, TH>(vs, p, tile);
+    static_assert(NB % NT == 0 || NT % NB == 0, "whole staging slots per thread");
+    using P = Px<PPL>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    const int view = view_of_tile(vs, tile);
+    const ViewRec& cam = vs.v[view];
+    const uint32_t lt = tile - cam.tile_off;
+    const int X0 = (int)(lt % (uint32_t)cam.gx) * TW, Y0 = (int)(lt / (uint32_t)cam.gx) * TH;
+    uint2 rg = p.ranges[tile];
+    uint32_t start = rg.x, count = rg.y - rg.x;
     // the tile's list must lie inside the sorted instances (checked build; it
     // assumes the status words of the lgs_sort call that made the lists)
-    if (!LGS_CHECK(t.start <= t.start + t.count &&
-                   (t.count == 0 || (int64_t)t.start + t.count <= p.status[LGS_ST_NUM_INSTANCES]), 20, p.status))
-        t.count = 0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool global_frame = VAR == VAR_GLOBAL;
-    const float Ox = global_frame ? 0.f : (float)t.X0 + 0.5f * (TW - 1);
-    const float Oy = global_frame ? 0.f : (float)t.Y0 + 0.5f * (TH - 1);
-    const float xl = global_frame ? (float)t.px : (float)t.lx - 0.5f * (TW - 1);
-    const float yl = global_frame ? (float)t.py : (float)t.ly - 0.5f * (TH - 1);
-    const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
+    if (!LGS_CHECK(start <= start + count &&
+                   (count == 0 || (int64_t)start + count <= p.status[LGS_ST_NUM_INSTANCES]), 20, p.status))
+        count = 0;
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !t.inside;
-    bool warp_done = __all_sync(0xffffffffu, done);
+    constexpr bool global_frame = VAR == VAR_GLOBAL;
+    const float Ox = global_frame ? 0.f : (float)X0 + 0.5f * (TW - 1);
+    const float Oy = global_frame ? 0.f : (float)Y0 + 0.5f * (TH - 1);
+    // the lane's pixels: tile-local (lx, ly[k]); basis B = [x'^2, x'y', y'^2, x', y', 1]
+    const int lx = (warp % Lay::NBX) * WX + lane % WX;
+    int ly[PPL];
+    bool inside[PPL];
+    P bx2, bxy, by2, bxl, byl, T, C0, C1, C2, thr;
+    uint32_t last[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        ly[k] = (warp / Lay::NBX) * WY + lane / WX + k * (WY / 2);
+        inside[k] = X0 + lx < cam.W && Y0 + ly[k] < cam.H;
+        const float xl = global_frame ? (float)(X0 + lx) : (float)lx - 0.5f * (TW - 1);
+        const float yl = global_frame ? (float)(Y0 + ly[k]) : (float)ly[k] - 0.5f * (TH - 1);
+        bx2[k] = xl * xl;
+        bxy[k] = xl * yl;
+        by2[k] = yl * yl;
+        bxl[k] = xl;
+        byl[k] = yl;
+        T[k] = 1.f;
+        C0[k] = 0.f;
+        C1[k] = 0.f;
+        C2[k] = 0.f;
+        // per-pixel 1/255 threshold in the log2 domain; +inf once the pixel
+        // has stopped (or lies outside the image), so that it never blends again
+        thr[k] = inside[k] ? LOG2_ALPHA_MIN : INF_F;
+        last[k] = 0;
+    }
+    auto lane_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) d = d && (VAR == VAR_LITERAL ? (!inside[k] || T[k] < 1e-4f) : thr[k] > 0.f);
+        return d;
+    };
+    bool warp_done = __all_sync(0xffffffffu, lane_done());
     uint32_t pairs = 0, cands = 0;
 
-    // Staging: thread i < NB copies the three 16-B records of list entry b0 + i
-    // with cp.async into buffer (b0 / NB) & 1, one batch ahead, so the gathers
-    // of batch b+1 are in flight while batch b blends. A thread reads back only
-    // the slots it copied itself, so its own group fence orders them.
+    // Staging: thread t copies the three 16-B records of list entries b0 + t,
+    // b0 + t + NT, ... with cp.async into buffer (b0 / NB) & 1, one batch ahead,
+    // so the gathers of batch b+1 are in flight while batch b blends. A thread
+    // reads back only the slots it copied itself, so its own group fence orders them.
     const int ti = threadIdx.x;
     auto stage = [&](uint32_t b, int buf) {
-        const uint32_t jj = b + (uint32_t)ti;
-        if (ti < NB && jj < t.count) {
-            const uint32_t id = p.vals[t.start + jj];
-            cp_async16(&S.raw[buf][0][ti], p.xy + id);
-            cp_async16(&S.raw[buf][1][ti], p.conic + id);
-            cp_async16(&S.raw[buf][2][ti], p.rgb + id);
+#pragma unroll
+        for (int sl = ti; sl < NB; sl += NT) {
+            const uint32_t jj = b + (uint32_t)sl;
+            if (jj < count) {
+                const uint32_t id = p.vals[start + jj];
+                cp_async16(&S.raw[buf][0][sl], p.xy + id);
+                cp_async16(&S.raw[buf][1][sl], p.conic + id);
+                cp_async16(&S.raw[buf][2][sl], p.rgb + id);
+            }
         }
         cp_async_commit();
     };
-    if (t.count > 0 && !__syncthreads_and(warp_done)) stage(0, 0);
+    if (count > 0 && !__syncthreads_and(warp_done)) stage(0, 0);
     int buf = 0;
-    for (uint32_t b0 = 0; b0 < t.count; b0 += NB, buf ^= 1) {
+    for (uint32_t b0 = 0; b0 < count; b0 += NB, buf ^= 1) {
         if (__syncthreads_and(warp_done)) break;
-        if (b0 + NB < t.count) stage(b0 + NB, buf ^ 1);
+        if (b0 + NB < count) stage(b0 + NB, buf ^ 1);
         else cp_async_commit();
         cp_async_wait<1>();
-        const uint32_t j = b0 + threadIdx.x;
-        if (ti < NB && j < t.count) {
-            const float4 xy = S.raw[buf][0][ti];
-            const float4 co = S.raw[buf][1][ti];
-            const float4 col = S.raw[buf][2][ti];
-            const float dx = __fadd_rn(xy.x - Ox, xy.z);
-            const float dy = __fadd_rn(xy.y - Oy, xy.w);
-            const float Dn = fmaf(co.x, dx, co.y * dy);
-            const float En = fmaf(co.y, dx, co.z * dy);
-            const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
-            sV[threadIdx.x] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
-                                          fmaf(Fn, LOG2E, __log2f(co.w)));
-            sDE[threadIdx.x] = make_float2(Dn * LOG2E, En * LOG2E);
-            sC[threadIdx.x] = col;
-            sM[threadIdx.x] = (uint8_t)warp_mask<TW, TH>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
-                                                         __fadd_rn(xy.y, xy.w), t.X0, t.Y0);
+#pragma unroll
+        for (int sl = ti; sl < NB; sl += NT) {
+            if (b0 + (uint32_t)sl < count) {
+                const float4 xy = S.raw[buf][0][sl];
+                const float4 co = S.raw[buf][1][sl];
+                const float4 col = S.raw[buf][2][sl];
+                const float dx = __fadd_rn(xy.x - Ox, xy.z);
+                const float dy = __fadd_rn(xy.y - Oy, xy.w);
+                const float Dn = fmaf(co.x, dx, co.y * dy);
+                const float En = fmaf(co.y, dx, co.z * dy);
+                const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
+                S.sV[sl] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
+                                       fmaf(Fn, LOG2E, __log2f(co.w)));
+                S.sDE[sl] = make_float2(Dn * LOG2E, En * LOG2E);
+                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, 0.f);
+                S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
+                                                               __fadd_rn(xy.y, xy.w), X0, Y0);
+            }
         }
         __syncthreads();
-        const int nb = (int)min((uint32_t)NB, t.count - b0);
+        const int nb = (int)min((uint32_t)NB, count - b0);
         if (COUNT && !warp_done) cands += (uint32_t)nb;
         if (!warp_done) {
             // compact the warp's list: the batch indices whose mask bit for this
@@ -209,7 +287,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
             int nl = 0;
             for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
-                const bool hit = jj < nb && ((sM[jj] >> warp) & 1u);
+                const bool hit = jj < nb && ((S.sM[jj] >> warp) & 1u);
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                 if (hit) sL[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
                 nl += __popc(bal);
@@ -222,71 +300,91 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 for (int i = i0; i < iend; ++i) {
                     const int g = sL[i];
                     if (VAR == VAR_LITERAL) {
-                        if (__all_sync(0xffffffffu, !t.inside || T < 1e-4f)) { done = true; break; }
+                        if (__all_sync(0xffffffffu, lane_done())) { warp_done = true; break; }
                         if (COUNT) ++pairs;
                     } else if (COUNT) {
-                        if (__all_sync(0xffffffffu, done)) break;
+                        if (__all_sync(0xffffffffu, lane_done())) break;
                         ++pairs;
                     }
-                    const float4 V = sV[g];
-                    const float2 DE = sDE[g];
-                    const float4 col = sC[g];
-                    const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
-                                     fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
-                    const float al = fminf(0.99f, ex2_approx(pw));
+                    const float4 V = S.sV[g];
+                    const float2 DE = S.sDE[g];
+                    const float4 ncol = S.sC[g];
+                    const uint32_t idx = b0 + (uint32_t)g + 1u;
+                    const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
+                                 pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
+                    // -alpha = -min(0.99, 2^pw), negated so that the packed
+                    // updates below need no separate negation
+                    P nal;
+#pragma unroll
+                    for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, -ex2_approx(pw[k]));
                     if (VAR == VAR_LITERAL) {
-                        const float w = al * T;
-                        C0 = fmaf(col.x, w, C0);
-                        C1 = fmaf(col.y, w, C1);
-                        C2 = fmaf(col.z, w, C2);
-                        T = T - w;
-                        last = b0 + (uint32_t)g + 1u;
+                        const P nw = pmul(nal, T);          // -w = -alpha T
+                        C0 = pfma(bcast<PPL>(ncol.x), nw, C0);
+                        C1 = pfma(bcast<PPL>(ncol.y), nw, C1);
+                        C2 = pfma(bcast<PPL>(ncol.z), nw, C2);
+                        T = padd(T, nw);                    // T - w
+#pragma unroll
+                        for (int k = 0; k < PPL; ++k) last[k] = idx;
                         continue;
                     }
-                    const bool valid = !done && pw >= LOG2_ALPHA_MIN;
-                    const float tT = fmaf(-al, T, T);
-                    const bool stop = valid && tT < 1e-4f;
-                    const bool blend = valid && !stop;
-                    done = done || stop;
-                    // alpha of the pixel's blend (0 when it does not blend): the
-                    // colour and T updates need no further select, and
-                    // fma(-0, T, T) leaves T exactly as it was
-                    const float ab = blend ? al : 0.f;
-                    const float w = ab * T;
-                    C0 = fmaf(col.x, w, C0);
-                    C1 = fmaf(col.y, w, C1);
-                    C2 = fmaf(col.z, w, C2);
-                    T = fmaf(-ab, T, T);
-                    last = blend ? (b0 + (uint32_t)g + 1u) : last;
+                    const P tT = pfma(nal, T, T);           // T (1 - alpha), one rounding
+                    P nab;
+#pragma unroll
+                    for (int k = 0; k < PPL; ++k) {
+                        const bool valid = pw[k] >= thr[k];
+                        const bool blend = valid && tT[k] >= 1e-4f;
+                        thr[k] = (valid && !blend) ? INF_F : thr[k];
+                        // -alpha of the pixel's blend, 0 when it does not blend:
+                        // the colour and T updates need no further select
+                        nab[k] = blend ? nal[k] : 0.f;
+                        last[k] = blend ? idx : last[k];
+                    }
+                    const P nw = pmul(nab, T);              // -w
+                    C0 = pfma(bcast<PPL>(ncol.x), nw, C0);  // (-c)(-w) = c w exactly
+                    C1 = pfma(bcast<PPL>(ncol.y), nw, C1);
+                    C2 = pfma(bcast<PPL>(ncol.z), nw, C2);
+                    T = pfma(nab, T, T);                    // T - alpha T, or T unchanged
                 }
-                if (__all_sync(0xffffffffu, done)) warp_done = true;
+                if (__all_sync(0xffffffffu, lane_done())) warp_done = true;
             }
         }
         __syncthreads();
     }
     cp_async_wait<0>();
-    write_pixel(vs, p, t, C0, C1, C2, T, last);
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (!inside[k]) continue;
+        const int64_t plane = (int64_t)cam.W * cam.H;
+        const int64_t pix = (int64_t)(Y0 + ly[k]) * cam.W + (X0 + lx);
+        float* o = p.out_rgb + 3 * (int64_t)cam.pix_off;
+        o[pix] = fmaf(T[k], cam.bg[0], C0[k]);
+        o[plane + pix] = fmaf(T[k], cam.bg[1], C1[k]);
+        o[2 * plane + pix] = fmaf(T[k], cam.bg[2], C2[k]);
+        p.out_T[cam.pix_off + pix] = T[k];
+        p.out_n[cam.pix_off + pix] = last[k];
+    }
     if (COUNT && lane == 0 && pairs)
         atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_PAIRS),
-                  (unsigned long long)pairs * 32ull);
+                  (unsigned long long)pairs * 32ull * PPL);
     if (COUNT && lane == 0 && cands)
         atomicAdd(reinterpret_cast<unsigned long long*>(p.status + LGS_ST_CANDIDATES),
                   (unsigned long long)cands);
 }
 
 // One CTA per tile.
-template <int TW, int TH, bool COUNT, int VAR = VAR_CONTRACT, int NB = BATCH>
-__global__ void __launch_bounds__(256) render_localgs(RenderParams p, Views vs) {
-    __shared__ LocalSmem S;
-    localgs_tile<TW, TH, COUNT, VAR, NB>(p, vs, blockIdx.x, S);
+template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
+__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_localgs(RenderParams p, Views vs) {
+    __shared__ LocalSmem<NB> S;
+    localgs_tile<TW, TH, WX, WY, COUNT, VAR, NB>(p, vs, blockIdx.x, S);
 }
 
 // Persistent CTAs: each pulls the next tile index from a work-queue counter
 // (status word LGS_ST_QUEUE, zeroed by the launcher) until all tiles are taken,
 // so uneven tile lists and uneven view sizes balance across the SMs.
-template <int TW, int TH, bool COUNT, int NB = BATCH>
-__global__ void __launch_bounds__(256) render_localgs_persistent(RenderParams p, Views vs) {
-    __shared__ LocalSmem S;
+template <int TW, int TH, int WX, int WY, bool COUNT, int NB>
+__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_localgs_persistent(RenderParams p,
+                                                                                     Views vs) {
+    __shared__ LocalSmem<NB> S;
     __shared__ uint32_t s_tile;
     unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE);
     for (;;) {
@@ -295,7 +393,7 @@ __global__ void __launch_bounds__(256) render_localgs_persistent(RenderParams p,
         const uint32_t tile = s_tile;
         __syncthreads();
         if (tile >= vs.n_tiles) break;
-        localgs_tile<TW, TH, COUNT, VAR_CONTRACT, NB>(p, vs, tile, S);
+        localgs_tile<TW, TH, WX, WY, COUNT, VAR_CONTRACT, NB>(p, vs, tile, S);
         __syncthreads();
     }
 }
@@ -352,15 +450,16 @@ __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
                   (unsigned long long)pairs * 32ull);
 }
 
-// The Local-GS contract kernel for one staging batch size (one CTA per tile or
-// persistent CTAs pulling tiles from the work queue).
-template <int TW, int TH, int NB>
+// The Local-GS contract kernel for one warp layout and staging batch size
+// (one CTA per tile, or persistent CTAs pulling tiles from the work queue).
+template <int TW, int TH, int WX, int WY, int NB>
 lgs_status launch_contract(const RenderParams& p, const Views& vs, bool count, bool persistent,
                            cudaStream_t s) {
-    const dim3 grid(vs.n_tiles), block(256);
+    constexpr int NT = Layout<TW, TH, WX, WY>::NT;
+    const dim3 grid(vs.n_tiles), block(NT);
     if (!persistent) {
-        if (count) render_localgs<TW, TH, true, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
-        else       render_localgs<TW, TH, false, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
+        if (count) render_localgs<TW, TH, WX, WY, true, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
+        else       render_localgs<TW, TH, WX, WY, false, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
         return cuda_status(cudaGetLastError());
     }
     if (cudaMemsetAsync(p.status + LGS_ST_QUEUE, 0, sizeof(int64_t), s) != cudaSuccess) return LGS_ERR_CUDA;
@@ -368,38 +467,54 @@ lgs_status launch_contract(const RenderParams& p, const Views& vs, bool count, b
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (count) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, true, NB>, 256, 0);
+        auto k = render_localgs_persistent<TW, TH, WX, WY, true, NB>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, 0);
         const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
-        render_localgs_persistent<TW, TH, true, NB><<<g, block, 0, s>>>(p, vs);
+        k<<<g, block, 0, s>>>(p, vs);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_localgs_persistent<TW, TH, false, NB>, 256, 0);
+        auto k = render_localgs_persistent<TW, TH, WX, WY, false, NB>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, 0);
         const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
-        render_localgs_persistent<TW, TH, false, NB><<<g, block, 0, s>>>(p, vs);
+        k<<<g, block, 0, s>>>(p, vs);
     }
     return cuda_status(cudaGetLastError());
 }
 
+template <int TW, int TH, int WX, int WY>
+lgs_status launch_layout(const RenderParams& p, const Views& vs, int batch, bool count, bool persistent,
+                         cudaStream_t s) {
+    if (batch == 64) return launch_contract<TW, TH, WX, WY, 64>(p, vs, count, persistent, s);
+    if (batch == 128) return launch_contract<TW, TH, WX, WY, 128>(p, vs, count, persistent, s);
+    return launch_contract<TW, TH, WX, WY, 256>(p, vs, count, persistent, s);
+}
+
+// The study variants (literal, global frame) run in the paper's layout.
+template <int TW, int TH, int VAR>
+lgs_status launch_variant(const RenderParams& p, const Views& vs, bool count, cudaStream_t s) {
+    constexpr int WX = TW, WY = TH / 8;
+    const dim3 grid(vs.n_tiles), block(Layout<TW, TH, WX, WY>::NT);
+    if (count) render_localgs<TW, TH, WX, WY, true, VAR, BATCH><<<grid, block, 0, s>>>(p, vs);
+    else       render_localgs<TW, TH, WX, WY, false, VAR, BATCH><<<grid, block, 0, s>>>(p, vs);
+    return cuda_status(cudaGetLastError());
+}
+
 template <int TW, int TH>
-lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, int batch, bool count,
-                         bool persistent, cudaStream_t s) {
-    const dim3 grid(vs.n_tiles), block(256);
+lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, int batch, int wx, int wy,
+                         bool count, bool persistent, cudaStream_t s) {
     if (mode == LGS_MODE_PLAIN) {
+        const dim3 grid(vs.n_tiles), block(256);
         if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
         else       render_plain<TW, TH, false><<<grid, block, 0, s>>>(p, vs);
-    } else if (mode == LGS_MODE_LITERAL) {
-        if (count) render_localgs<TW, TH, true, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
-        else       render_localgs<TW, TH, false, VAR_LITERAL><<<grid, block, 0, s>>>(p, vs);
-    } else if (mode == LGS_MODE_GLOBAL) {
-        if (count) render_localgs<TW, TH, true, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
-        else       render_localgs<TW, TH, false, VAR_GLOBAL><<<grid, block, 0, s>>>(p, vs);
-    } else if (batch == 64) {
-        return launch_contract<TW, TH, 64>(p, vs, count, persistent, s);
-    } else if (batch == 128) {
-        return launch_contract<TW, TH, 128>(p, vs, count, persistent, s);
-    } else {
-        return launch_contract<TW, TH, 256>(p, vs, count, persistent, s);
+        return cuda_status(cudaGetLastError());
     }
-    return cuda_status(cudaGetLastError());
+    if (mode == LGS_MODE_LITERAL) return launch_variant<TW, TH, VAR_LITERAL>(p, vs, count, s);
+    if (mode == LGS_MODE_GLOBAL) return launch_variant<TW, TH, VAR_GLOBAL>(p, vs, count, s);
+    if (wx == TW && wy == TH / 8) return launch_layout<TW, TH, TW, TH / 8>(p, vs, batch, count, persistent, s);
+    if constexpr (TW == 16) {
+        if (wx == 8 && wy == 4) return launch_layout<16, 16, 8, 4>(p, vs, batch, count, persistent, s);
+        if (wx == 16 && wy == 4) return launch_layout<16, 16, 16, 4>(p, vs, batch, count, persistent, s);
+    }
+    return launch_layout<TW, TH, 8, 8>(p, vs, batch, count, persistent, s);
 }
 
 }  // namespace lgs
@@ -434,8 +549,11 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     p.status = d_status;
     const bool count = (cfg->flags & LGS_FLAG_COUNT) != 0;
     const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
+    int wx = 0, wy = 0;
+    if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
+    if (cfg->mode != LGS_MODE_LOCALGS && (wx != cfg->tile_w || wy != cfg->tile_h / 8)) return LGS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, batch, count, persistent, s);
-    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, batch, count, persistent, s);
-    return launch_render<32, 8>(p, vs, cfg->mode, batch, count, persistent, s);
+    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    return launch_render<32, 8>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
 }

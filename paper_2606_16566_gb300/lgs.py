@@ -27,12 +27,25 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def config(tile=(16, 16), mode="localgs", flags=0, batch=0) -> L.lgs_config:
+# warp blocks of the Local-GS render per tile shape (the first is the paper's layout)
+WARP_BLOCKS = {(16, 16): ((16, 2), (8, 4), (16, 4), (8, 8)), (8, 32): ((8, 4), (8, 8)),
+               (32, 8): ((32, 1), (8, 8))}
+
+
+def config(tile=(16, 16), mode="localgs", flags=0, batch=0, block=None) -> L.lgs_config:
+    """lgs_config; block = (warp_w, warp_h) of the Local-GS render, None = the
+    paper's full-width strips."""
     if tuple(tile) not in _TILES:
         raise ValueError(f"tile shape {tile} not in {_TILES}")
     m = {"localgs": L.MODE_LOCALGS, "plain": L.MODE_PLAIN, "literal": L.MODE_LITERAL,
          "global": L.MODE_GLOBAL}[mode]
-    return L.lgs_config(int(tile[0]), int(tile[1]), m, int(batch), int(flags))
+    wx, wy = (0, 0) if block is None else (int(block[0]), int(block[1]))
+    return L.lgs_config(int(tile[0]), int(tile[1]), m, int(batch), int(flags), wx, wy)
+
+
+def with_flags(cfg: L.lgs_config, flags) -> L.lgs_config:
+    """A copy of cfg with other flags."""
+    return L.lgs_config(cfg.tile_w, cfg.tile_h, cfg.mode, cfg.batch, int(flags), cfg.warp_w, cfg.warp_h)
 
 
 def cameras(cams) -> ctypes.Array:

@@ -490,3 +490,113 @@ def test_localgs_pairs_stop_at_the_warps_last_stop_position():
     assert np.all(r["n_contrib"] == 3)
     assert r["ranges"][0][1] - r["ranges"][0][0] == n
     assert oracle.localgs_pairs(r, cam) == 8 * 4 * 32
+
+
+@pytest.mark.parametrize("block", [(8, 4), (8, 8), (16, 4), (4, 8)])
+def test_block_mask_equals_exact_row_intersection_per_block_column(block):
+    """2D warp blocks: the bit of block (bx, by) is set iff one of the block's
+    integer rows meets the ellipse inside the block's own column range."""
+    bw, bh = block
+    rng = np.random.default_rng(43 + bw + bh)
+    nbx, nby = 16 // bw, 16 // bh
+    checked = 0
+    for _ in range(1500):
+        L = rng.standard_normal((2, 2)) * rng.uniform(0.05, 1.0)
+        Q = np.linalg.inv(L @ L.T * rng.uniform(1, 60) + 0.3 * np.eye(2))
+        a, b, c = Q[0, 0], Q[0, 1], Q[1, 1]
+        o = rng.uniform(0.003, 0.99)
+        X0, Y0 = 32, 48
+        mux, muy = rng.uniform(X0 - 30, X0 + 46), rng.uniform(Y0 - 30, Y0 + 46)
+        m = oracle.block_mask(a, b, c, o, mux, muy, X0, Y0, 16, 16, bw, bh)
+        tau = 2 * math.log(255 * o)
+        refs = []
+        for e in (0.0, -1e-7, 1e-7):
+            ref = 0
+            if tau > 0:
+                for bx in range(nbx):
+                    x0, x1 = X0 + bx * bw - mux, X0 + bx * bw + bw - 1 - mux
+                    for row in range(16):
+                        if _row_hits(a, b, c, tau, x0, x1, Y0 + row + e - muy):
+                            ref |= 1 << ((row // bh) * nbx + bx)
+            refs.append(ref)
+        if len(set(refs)) != 1:
+            continue
+        checked += 1
+        assert m == refs[0], (block, a, b, c, o, mux, muy, m, refs[0])
+    assert checked > 1400
+
+
+@pytest.mark.parametrize("block", [(8, 4), (8, 8)])
+def test_block_mask_is_superset_of_contributing_pixels(block):
+    bw, bh = block
+    rng = np.random.default_rng(44)
+    nbx = 16 // bw
+    for _ in range(400):
+        L = rng.standard_normal((2, 2)) * rng.uniform(0.05, 1.0)
+        Q = np.linalg.inv(L @ L.T * rng.uniform(1, 60) + 0.3 * np.eye(2))
+        a, b, c = Q[0, 0], Q[0, 1], Q[1, 1]
+        o = rng.uniform(0.003, 0.99)
+        X0, Y0 = 16, 16
+        mux, muy = rng.uniform(0, 48), rng.uniform(0, 48)
+        m = oracle.block_mask(a, b, c, o, mux, muy, X0, Y0, 16, 16, bw, bh)
+        yy, xx = np.mgrid[Y0:Y0 + 16, X0:X0 + 16]
+        dx, dy = xx - mux, yy - muy
+        al = o * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+        for r, cc in zip(*np.nonzero(al >= 1 / 255 * (1 + 1e-12))):
+            assert m & (1 << ((r // bh) * nbx + cc // bw))
+
+
+def test_block_mask_with_full_width_blocks_is_the_strip_mask():
+    rng = np.random.default_rng(45)
+    for _ in range(300):
+        L = rng.standard_normal((2, 2)) * rng.uniform(0.05, 1.0)
+        Q = np.linalg.inv(L @ L.T * rng.uniform(1, 60) + 0.3 * np.eye(2))
+        a, b, c = Q[0, 0], Q[0, 1], Q[1, 1]
+        o = rng.uniform(0.003, 0.99)
+        mux, muy = rng.uniform(0, 48), rng.uniform(0, 48)
+        assert oracle.block_mask(a, b, c, o, mux, muy, 16, 16, 16, 16, 16, 2) == \
+            oracle.warp_mask(a, b, c, o, mux, muy, 16, 16)
+
+
+@pytest.mark.parametrize("block", [(8, 4), (8, 8), (16, 4)])
+def test_localgs_pairs_blocks_single_gaussian_and_stack(block):
+    """The block count: one Gaussian, no stop -> (blocks whose rows meet its
+    ellipse inside their own column range) x block pixels, summed over the
+    tiles of its list; the alpha ~ 0.95 stack -> every block counted for the
+    first 4 Gaussians: 4 x 256 = 1024 pairs per 16x16 tile, any block shape."""
+    bw, bh = block
+    nbx = 16 // bw
+    rng = np.random.default_rng(62)
+    cam = _axis_camera(96, 96, 100.0)
+    checked = 0
+    for trial in range(30):
+        sc = _scene([[*rng.uniform(-1.0, 1.0, 2), 4.0]], [rng.uniform(0.02, 0.12, 3)],
+                    [rng.standard_normal(4)], [rng.uniform(0.05, 0.6)], [[[0.2, 0.2, 0.2]]])
+        r = oracle.render(sc, cam)
+        pre = r["pre"]
+        a, b, c = pre["conic"][0]
+        tau = 2 * math.log(255 * float(np.float32(sc["opacities"][0])))
+        mux, muy = pre["uv"][0]
+        ref, ambiguous = 0, False
+        for t in range(36):
+            st, en = r["ranges"][t]
+            if en <= st:
+                continue
+            X0, Y0 = (t % 6) * 16, (t // 6) * 16
+            for w in range(256 // (bw * bh)):
+                bx, by = w % nbx, w // nbx
+                x0, x1 = X0 + bx * bw - mux, X0 + bx * bw + bw - 1 - mux
+                hits = [any(_row_hits(a, b, c, tau, x0, x1, Y0 + by * bh + k + e - muy) for k in range(bh))
+                        for e in (0.0, -1e-7, 1e-7)]
+                ambiguous |= len(set(hits)) != 1
+                ref += bw * bh * hits[0]
+        if ambiguous or tau <= 0:
+            continue
+        assert oracle.localgs_pairs(r, cam, block=block) == ref, trial
+        checked += 1
+    assert checked >= 20
+    cam16 = _axis_camera(16, 16, 100.0)
+    n = 5
+    st = _scene([[0, 0, 2.0 + 0.5 * k] for k in range(n)], [[1.0] * 3] * n, [[1, 0, 0, 0]] * n,
+                [0.95] * n, [[[0.1 * k, 0.1, 0.1]] for k in range(n)])
+    assert oracle.localgs_pairs(oracle.render(st, cam16), cam16, block=block) == 4 * 256
