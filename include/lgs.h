@@ -135,6 +135,11 @@ typedef struct {
  * shrink. lgs_sort then also reads pre->xy and pre->conic. The other entry
  * points ignore the flag (they follow the lists they are given). */
 #define LGS_FLAG_TIGHT 4
+/* lgs_sort: run every radix pass as one single-kernel "onesweep" pass
+ * (decoupled look-back over earlier blocks' digit counts) instead of the
+ * default three fully parallel reduce-then-scan kernels. Results are
+ * identical; only the speed differs. */
+#define LGS_FLAG_ONESWEEP 8
 
 /* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}), render mode and flags.
  * batch = Gaussians the Local-GS render (LGS_MODE_LOCALGS) stages in shared

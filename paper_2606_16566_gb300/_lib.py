@@ -35,6 +35,7 @@ MODE_GLOBAL = 3
 FLAG_COUNT = 1
 FLAG_PERSISTENT = 2
 FLAG_TIGHT = 4
+FLAG_ONESWEEP = 8
 PROBE_FFMA, PROBE_FFMA2, PROBE_EX2 = 0, 1, 2
 
 _vp = ctypes.c_void_p

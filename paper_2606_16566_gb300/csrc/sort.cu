@@ -83,6 +83,8 @@ __device__ __forceinline__ int64_t pass_count(const int64_t* cnt, int64_t n) {
     return k > n ? 0 : k;
 }
 
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 __device__ __forceinline__ int64_t sort_count(const int64_t* status, int64_t capacity) {
     return pass_count(status + LGS_ST_NUM_INSTANCES, capacity);
 }
@@ -749,6 +751,194 @@ __global__ void __launch_bounds__(OS_THREADS, 2) onesweep_pass(
     }
 }
 
+// ------------------------------------------------------------------ radix passes (reduce-then-scan)
+// The same stable LSD pass as onesweep_pass, split so that no block ever waits
+// on another: rs_upsweep counts each 4096-element block's digits into a
+// digit-major table counts[d * nb + b]; rs_scan turns every row d into the
+// global output position of block b's first element of digit d (an exclusive
+// scan along the row plus the digit's base from the histogram kernels); and
+// rs_downsweep ranks its block's keys stably (the warp-ballot ranking of
+// onesweep_pass) and scatters them to those positions. The keys are read twice
+// (4 B per element more traffic than onesweep), but every kernel runs fully
+// parallel instead of along a look-back chain. Keys are u32 or, for tile ids
+// of at most 2^16 tiles, u16.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 4096
+
+template <typename KT>
+struct RsSrc {
+    const KT* k;             // keys (nullptr: synthesized from tiles and depth, u32 only)
+    const uint32_t* v;
+    const uint32_t* tiles;
+    const float* depth;
+};
+
+template <typename KT>
+__device__ __forceinline__ bool rs_load(const RsSrc<KT>& src, int64_t i, uint32_t& k, uint32_t& v) {
+    if (src.k) {
+        k = (uint32_t)src.k[i];
+        v = src.v ? src.v[i] : 0u;
+        return true;
+    }
+    v = (uint32_t)i;
+    const uint32_t tiles = src.tiles[i];
+    const uint32_t bits = __float_as_uint(src.depth[i]);
+    k = tiles ? bits : 0xffffffffu;
+    return tiles != 0u;
+}
+
+// Per-block digit counts. Each warp counts its 512 elements into a private
+// histogram (one atomic for a whole warp when its 32 kept digits agree).
+template <typename KT>
+__global__ void __launch_bounds__(RS_THREADS) rs_upsweep(RsSrc<KT> src, const int64_t* cnt, int64_t count,
+                                                         int shift, uint32_t* counts, int64_t nb) {
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ uint32_t h[NW][RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < RADIX; d += 32) h[warp][d] = 0;
+    const int64_t K = pass_count(cnt, count);
+    const int64_t first = (int64_t)blockIdx.x * RS_TILE;
+    if (first >= K) return;
+    __syncwarp();
+    const int64_t wfirst = first + warp * (RS_TILE / NW);
+#pragma unroll 4
+    for (int i = 0; i < RS_TILE / NW / 32; ++i) {
+        const int64_t j = wfirst + i * 32 + lane;
+        uint32_t k = 0, v;
+        const bool ok = j < K && rs_load(src, j, k, v);
+        const uint32_t d = (k >> shift) & 0xffu;
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (bal == 0u) continue;
+        const int leader = __ffs(bal) - 1;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, leader);
+        if (__all_sync(0xffffffffu, !ok || d == d0)) {
+            if (lane == leader) h[warp][d0] += (uint32_t)__popc(bal);
+        } else if (ok) {
+            atomicAdd(&h[warp][d], 1u);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += h[w][d];
+        counts[(int64_t)d * nb + blockIdx.x] = t;
+    }
+}
+
+// Row d of the count table -> exclusive prefix along the live blocks + the
+// digit's base (one CTA per digit).
+__global__ void __launch_bounds__(1024) rs_scan(uint32_t* counts, int64_t nb, const int64_t* cnt, int64_t count,
+                                               const uint32_t* bases) {
+    __shared__ uint32_t ws[32];
+    const int64_t K = pass_count(cnt, count);
+    const int64_t live = ceil_div_dev(K, RS_TILE);
+    uint32_t* row = counts + (int64_t)blockIdx.x * nb;
+    uint32_t carry = bases[blockIdx.x];
+    for (int64_t b0 = 0; b0 < live; b0 += 1024) {
+        const int64_t b = b0 + threadIdx.x;
+        const uint32_t v = b < live ? row[b] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<1024>(v, ws, tot);
+        if (b < live) row[b] = carry + ex;
+        carry += tot;
+    }
+}
+
+template <typename KT>
+struct RsSmem {
+    uint32_t cnt[RS_THREADS / 32][RADIX];   // per-warp digit counters -> (digit, warp) offsets
+    uint32_t ws[32];
+    uint32_t start[RADIX];   // block-local start of each digit
+    uint32_t base[RADIX];    // global output position of each digit's first element in this block
+    KT keys[RS_TILE];
+    uint32_t vals[RS_TILE];
+};
+
+template <typename KT>
+__global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT* __restrict__ kout,
+                                                              uint32_t* __restrict__ vout, const int64_t* cnt,
+                                                              int64_t count, int shift, const uint32_t* offsets,
+                                                              int64_t nb, int64_t* err_status) {
+    constexpr int NW = RS_THREADS / 32;
+    constexpr int PER_WARP = RS_TILE / NW;      // 512
+    __shared__ RsSmem<KT> S;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t K = pass_count(cnt, count);
+    const int64_t first = (int64_t)blockIdx.x * RS_TILE;
+    if (first >= K) return;
+    for (int d = lane; d < RADIX; d += 32) S.cnt[warp][d] = 0;
+    S.base[t] = offsets[(int64_t)t * nb + blockIdx.x];
+    const int n_valid = (int)min((int64_t)RS_TILE, K - first);
+    // keys first; the values are loaded only once their slots are known, so
+    // they hold no registers through the ranking
+    uint32_t k[RS_ITEMS];
+    uint32_t keep = 0;      // bit i: item i is a kept element
+    const int wbase = warp * PER_WARP;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const int j = wbase + i * 32 + lane;
+        k[i] = 0xffffffffu;
+        uint32_t unused;
+        if (j < n_valid && rs_load(RsSrc<KT>{src.k, nullptr, src.tiles, src.depth}, first + j, k[i], unused))
+            keep |= 1u << i;
+    }
+    __syncwarp();
+    // stable rank of every kept key among equal digits of its warp's range
+    // (one ballot per digit bit; bit 8 marks a dropped element)
+    uint16_t rk[RS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const uint32_t d = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
+        const uint32_t b = d < 0x100u ? S.cnt[warp][d] : 0u;
+        rk[i] = (uint16_t)(b + __popc(peers & lt));
+        __syncwarp();
+        if (d < 0x100u && (peers >> lane) == 1u) S.cnt[warp][d] = b + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t pre[NW], acc = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        pre[w] = acc;
+        acc += S.cnt[w][t];
+    }
+    uint32_t n_kept;
+    const uint32_t st = block_exclusive_scan<RS_THREADS>(acc, S.ws, n_kept);
+    S.start[t] = st;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) S.cnt[w][t] = st + pre[w];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        if (keep & (1u << i)) {
+            const uint32_t pos = S.cnt[warp][(k[i] >> shift) & 0xffu] + rk[i];
+            const int64_t j = first + wbase + i * 32 + lane;
+            S.keys[pos] = (KT)k[i];
+            S.vals[pos] = src.k ? src.v[j] : (uint32_t)j;
+        }
+    }
+    __syncthreads();
+    for (int j = t; j < (int)n_kept; j += RS_THREADS) {
+        const uint32_t key = S.keys[j];
+        const uint32_t d = (key >> shift) & 0xffu;
+        const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
+        if (LGS_CHECK((int64_t)gpos < K, 9, err_status)) {
+            kout[gpos] = (KT)key;
+            vout[gpos] = S.vals[j];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ ranges
 // Per-tile [start, end) of the sorted tile ids; each thread takes 4
 // consecutive instances (one 16-B load when all 4 lie below K).
@@ -849,7 +1039,11 @@ constexpr SortWsOffsets sort_ws_offsets(int64_t m, int64_t capacity) {
     o.ak = off;         off += align_up(sizeof(uint32_t) * cap);
     o.bk = off;         off += align_up(sizeof(uint32_t) * cap);
     o.bv = off;         off += align_up(sizeof(uint32_t) * cap);
-    o.look = off;       off += align_up(sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1));
+    // look-back words of a onesweep pass, or the count table of a reduce-then-scan pass
+    const int64_t nr = ceil_div(m > capacity ? m : capacity, RS_TILE);
+    const size_t look_b = sizeof(uint64_t) * RADIX * (size_t)(nt > 0 ? nt : 1);
+    const size_t cnt_b = sizeof(uint32_t) * RADIX * (size_t)(nr > 0 ? nr : 1);
+    o.look = off;       off += align_up(look_b > cnt_b ? look_b : cnt_b);
     o.counters = off;   off += align_up(8 * sizeof(uint32_t));
     o.bases = off;      off += align_up(2 * OS_MAX_DIGITS * RADIX * sizeof(uint32_t));
     o.total = off;
@@ -898,15 +1092,29 @@ static void onesweep_prepare(const OsSrc& src, const int64_t* cnt, int64_t count
 
 // One stable LSD pass over u32 keys carrying u32 values (element count from
 // the device word `cnt` when given, else `count`; the grid covers `count`).
+// With `onesweep` one look-back kernel (onesweep_pass), else the three
+// reduce-then-scan kernels (rs_upsweep, rs_scan, rs_downsweep; their count
+// table reuses the look-back words' space, which no concurrent pass uses).
 static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const int64_t* cnt,
                        int64_t count, int shift, const uint32_t* bases, const SortWs* ws,
-                       int64_t* d_status, cudaStream_t s) {
-    const int64_t nt = ceil_div(count, OS_TILE);
-    if (nt == 0) return;
-    cudaMemsetAsync(ws->look, 0, sizeof(unsigned long long) * RADIX * (size_t)nt, s);
-    cudaMemsetAsync(ws->counters, 0, sizeof(uint32_t), s);
-    onesweep_pass<<<(unsigned)nt, OS_THREADS, sizeof(OneSmem), s>>>(
-        src, kout, vout, cnt, count, shift, bases, ws->look, ws->counters, d_status, OS_SPIN_LIMIT);
+                       int64_t* d_status, cudaStream_t s, bool onesweep) {
+    if (onesweep) {
+        const int64_t nt = ceil_div(count, OS_TILE);
+        if (nt == 0) return;
+        cudaMemsetAsync(ws->look, 0, sizeof(unsigned long long) * RADIX * (size_t)nt, s);
+        cudaMemsetAsync(ws->counters, 0, sizeof(uint32_t), s);
+        onesweep_pass<<<(unsigned)nt, OS_THREADS, sizeof(OneSmem), s>>>(
+            src, kout, vout, cnt, count, shift, bases, ws->look, ws->counters, d_status, OS_SPIN_LIMIT);
+        return;
+    }
+    const int64_t nb = ceil_div(count, RS_TILE);
+    if (nb == 0) return;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(ws->look);
+    const RsSrc<uint32_t> rs{src.k, src.v, src.tiles, src.depth};
+    rs_upsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, cnt, count, shift, counts, nb);
+    rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, cnt, count, bases);
+    rs_downsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift, counts, nb,
+                                                               d_status);
 }
 
 }  // namespace lgs
@@ -943,11 +1151,12 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     //    from tiles-touched and depth and drops the culled entries
     const OsSrc entries{nullptr, nullptr, pre->tiles, pre->depth};
     onesweep_prepare(entries, nullptr, m, 4, ws->bases, ws->mvis, s);
-    radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s);
+    const bool os = (vs->flags & LGS_FLAG_ONESWEEP) != 0;
+    radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s, os);
     uint32_t *k0 = ws->ek2, *v0 = ws->ev2, *k1 = ws->ek, *v1 = ws->ev;
     for (int shift = 8; shift < 32; shift += 8) {
         radix_pass(OsSrc{k0, v0, nullptr, nullptr}, k1, v1, ws->mvis, m, shift,
-                   ws->bases + RADIX * (shift / 8), ws, d_status, s);
+                   ws->bases + RADIX * (shift / 8), ws, d_status, s, os);
         uint32_t* t = k0; k0 = k1; k1 = t;
         t = v0; v0 = v1; v1 = t;
     }
@@ -1002,7 +1211,7 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     }
     for (int p = 0; p < passes; ++p) {
         radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p,
-                   tbases + p * RADIX, ws, d_status, s);
+                   tbases + p * RADIX, ws, d_status, s, os);
         uint32_t* t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }

@@ -112,6 +112,7 @@ def test_python_constants_match_the_header():
              "LGS_MODE_PLAIN": L.MODE_PLAIN, "LGS_MODE_LITERAL": L.MODE_LITERAL,
              "LGS_MODE_GLOBAL": L.MODE_GLOBAL, "LGS_FLAG_COUNT": L.FLAG_COUNT,
              "LGS_FLAG_PERSISTENT": L.FLAG_PERSISTENT, "LGS_FLAG_TIGHT": L.FLAG_TIGHT,
+             "LGS_FLAG_ONESWEEP": L.FLAG_ONESWEEP,
              "LGS_ST_NUM_INSTANCES": L.ST_NUM_INSTANCES, "LGS_ST_PAIRS": L.ST_PAIRS,
              "LGS_ST_CANDIDATES": L.ST_CANDIDATES, "LGS_PROBE_FFMA": L.PROBE_FFMA,
              "LGS_PROBE_FFMA2": L.PROBE_FFMA2, "LGS_PROBE_EX2": L.PROBE_EX2}

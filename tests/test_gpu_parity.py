@@ -290,3 +290,28 @@ def test_outdoor_full_size_views(v, tile, tight):
     assert prep["radius_mismatch"] == 0 and prep["tiles_mismatch"] == 0, prep
     assert prep["rect_mismatch"] == 0 and prep["depth_mismatch"] == 0, prep
     assert prep["differ"] <= max(2, 1e-4 * n), prep
+
+
+@pytest.mark.parametrize("tight", [False, True])
+@pytest.mark.parametrize("tile", TILES)
+def test_reduce_then_scan_equals_onesweep(tile, tight):
+    """The default radix passes (reduce-then-scan: upsweep, scan, downsweep) and
+    the single-kernel onesweep passes (LGS_FLAG_ONESWEEP) give identical keys,
+    values and tile ranges, on a multi-view batch whose entry and tile-id
+    passes both span many blocks."""
+    sc, cams = scenes.random_small(20000, seed=14, width=480, height=352, log_scale_mean=-2.5)
+    cams = cams + [scenes.look_at((2.0, 1.0, -4.0), (0, 0, 0), 333, 215, 55.0)]
+    g = lgs.to_device(sc)
+    out = []
+    for extra in (0, L.FLAG_ONESWEEP):
+        cfg = lgs.config(tile, "localgs", (L.FLAG_TIGHT if tight else 0) | extra)
+        st = lgs.new_status()
+        pre = lgs.preprocess(g, cams, cfg, status=st)
+        keys, vals, ranges = lgs.sort(pre, 20000, cams, cfg, 1 << 21, status=st)
+        s = lgs.read_status(st)
+        assert s[L.ST_CODE] == 0
+        K = int(s[L.ST_NUM_INSTANCES])
+        assert K > 100000
+        out.append((keys[:K].clone(), vals[:K].clone(), ranges.clone()))
+    for a, b in zip(*out):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
