@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--block", default="paper",
                    help="warp block WxH of the Local-GS render with a fixed --tile (paper = full-width strips)")
     p.add_argument("--no-tiny", action="store_true", help="skip the 10k-Gaussian 256x256 configuration")
+    p.add_argument("--sort", default="rts", choices=["rts", "onesweep"],
+                   help="with --profile: radix passes as reduce-then-scan kernels or onesweep kernels")
     return p.parse_args()
 
 
@@ -532,7 +534,8 @@ def run_ours(args, rank, world):
         probe = lgs.render(g, cams, tile=tile)
         pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
         del probe
-        cfg = lgs.config(tile, args.mode, L.FLAG_TIGHT if args.tight else 0, 0, block)
+        flags = (L.FLAG_TIGHT if args.tight else 0) | (L.FLAG_ONESWEEP if args.sort == "onesweep" else 0)
+        cfg = lgs.config(tile, args.mode, flags, 0, block)
         if args.backward:
             pipe.setup_backward()
         for _ in range(args.warmup + args.steps):

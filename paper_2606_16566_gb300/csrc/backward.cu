@@ -96,72 +96,93 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 // Per-warp buffer of the deferred reduction: up to RED_ROWS rows, one per
-// Gaussian of the warp's list, each holding the 32 lanes' dp and w. The 16-B
-// column group c of row r is stored at group c ^ (r & 7), so that the row
-// writes of the walk (32 lanes, one row) and the 16-B reads of the reduction
-// (8 rows, one column group each) both hit distinct banks.
+// Gaussian of the warp's list. Row r holds, per lane, (dp of its first pixel,
+// dp of its second pixel (0 with one pixel per lane), W_r, W_g) in R4 and W_b
+// in R1, where dp = dL/dalpha alpha of a pixel and W_c = sum over the lane's
+// pixels of w g_c (w = alpha T, g = dL/drgb). Lane c of row r is stored at
+// column c ^ (r & 7), so that the row writes of the walk (one row, 32 lanes)
+// and the reads of the reduction (8 rows, 8 lanes each) hit distinct banks.
 constexpr int RED_ROWS = 8;
 struct __align__(16) BwdRed {
-    float dp[RED_ROWS][32];
-    float w[RED_ROWS][32];
+    float4 R4[RED_ROWS][32];
+    float R1[RED_ROWS][32];
     uint32_t slot[RED_ROWS];   // batch index of the row's Gaussian
 };
 
-__device__ __forceinline__ int red_col(int row, int col) {
-    return ((((col >> 2) ^ row) & 7) << 2) | (col & 3);
-}
+template <int NW>
+struct BwdSmem {
+    float4 sV[BWD_BATCH];        // (A, B, C, F), log2 domain
+    float2 sDE[BWD_BATCH];       // (D, E)
+    float4 sC[BWD_BATCH];        // (r, g, b, list position + 1 as bits)
+    uint8_t sM[BWD_BATCH];       // warp-block mask
+    uint8_t sL[NW][BWD_BATCH];   // per warp: batch indices of its set mask bits
+    uint32_t sId[BWD_BATCH];
+    float sG[BWD_BATCH][9];      // per staged Gaussian: A, B, C, D, E, r, g, F, b gradients
+    uint32_t sLast[NW];
+    BwdRed red[NW];
+};
 
-// Reduces rows 0..ns-1 of the warp's buffer into sG. Lane (e, q) = (lane %
-// RED_ROWS, lane / RED_ROWS) sums row e over the RED_ROWS strip pixels starting
-// at q * RED_ROWS, in groups of 8 that each lie in one pixel row (the tile width
-// is a multiple of 8). A group centred on column xc of local row y has, with
-// offsets u = ii - 3.5, S0 = sum dp, Sx = xc S0 + sum dp u and
-// Sxx = xc^2 S0 + 2 xc sum dp u + sum dp u^2, and sum dp x y = y Sx,
-// sum dp y^2 = y^2 S0, sum dp y = y S0. Shuffles add the lanes of a row; lanes
-// 0..ns-1 then hold the warp's sums.
-template <int TW, int TH>
-__device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float4* gp, float (*sG)[9],
-                                            int lane, int warp) {
-    constexpr int PIX = RED_ROWS;   // pixels per lane
-    const int e = lane % RED_ROWS, q = lane / RED_ROWS;
+// Reduces rows 0..ns-1 of a warp's buffer into sG. Lane (e, q) = (lane % 8,
+// lane / 8) sums row e over the records of lanes 8q..8q+7, which own 8
+// consecutive pixel columns of one pixel row (the block width is a multiple
+// of 8): with offsets u = i - 3.5 from the group's centre column xc and the
+// group's rows y_k, the sums S0 = sum dp, S1 = sum dp u, S2 = sum dp u^2 of
+// each row k give the six hoisted moments (x'^2 -> xc^2 S0 + 2 xc S1 + S2,
+// x'y' -> y_k (xc S0 + S1), y'^2 -> y_k^2 S0, x' -> xc S0 + S1, y' -> y_k S0,
+// 1 -> S0); two shuffle levels add the four groups of a row and lanes 0..ns-1
+// hold the warp's sums.
+template <int TW, int TH, int WX, int WY>
+__device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, float (*sG)[9], int lane, int warp) {
+    using Lay = Layout<TW, TH, WX, WY>;
+    constexpr int PPL = Lay::PPL;
+    static_assert(WX % 8 == 0, "lane groups of 8 pixel columns");
+    const int e = lane & 7, q = lane >> 3;
+    const int bx = warp % Lay::NBX, by = warp / Lay::NBX;
+    const float xc = (float)(bx * WX + (8 * q) % WX) + 3.5f - 0.5f * (TW - 1);
+    float yk[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) yk[k] = (float)(by * WY + (8 * q) / WX + k * (WY / 2)) - 0.5f * (TH - 1);
     float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (e < ns) {
+        float S0[PPL], S1[PPL], S2[PPL];
 #pragma unroll
-        for (int sg = 0; sg < PIX / 8; ++sg) {
-            const int pb = q * PIX + 8 * sg;                 // first pixel of the group
-            const float xc = (float)(pb % TW) + 3.5f - 0.5f * (TW - 1);
-            const float y = (float)(warp * (TH / 8) + pb / TW) - 0.5f * (TH - 1);
-            const float4 d0 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, pb)]);
-            const float4 d1 = *reinterpret_cast<const float4*>(&R.dp[e][red_col(e, pb + 4)]);
-            const float4 w0 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, pb)]);
-            const float4 w1 = *reinterpret_cast<const float4*>(&R.w[e][red_col(e, pb + 4)]);
-            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-            const float ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-            float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        for (int k = 0; k < PPL; ++k) S0[k] = S1[k] = S2[k] = 0.f;
+        float W0 = 0.f, W1 = 0.f, W2 = 0.f;
 #pragma unroll
-            for (int ii = 0; ii < 8; ++ii) {
-                const float u = (float)ii - 3.5f;
-                S0 += d[ii];
-                S1 = fmaf(d[ii], u, S1);
-                S2 = fmaf(d[ii], u * u, S2);
-                const float4 g = gp[pb + ii];
-                v[5] = fmaf(ww[ii], g.x, v[5]);
-                v[6] = fmaf(ww[ii], g.y, v[6]);
-                v[8] = fmaf(ww[ii], g.z, v[8]);
+        for (int i = 0; i < 8; ++i) {
+            const int col = 8 * q + (i ^ e);
+            const float4 r4 = R.R4[e][col];
+            const float w2 = R.R1[e][col];
+            const float u = (float)i - 3.5f;
+            const float dpk[2] = {r4.x, r4.y};
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                S0[k] += dpk[k];
+                S1[k] = fmaf(dpk[k], u, S1[k]);
+                S2[k] = fmaf(dpk[k], u * u, S2[k]);
             }
-            const float Sx = fmaf(xc, S0, S1);
-            v[0] += fmaf(xc, fmaf(xc, S0, 2.f * S1), S2);
-            v[1] = fmaf(y, Sx, v[1]);
-            v[2] = fmaf(y * y, S0, v[2]);
-            v[3] += Sx;
-            v[4] = fmaf(y, S0, v[4]);
-            v[7] += S0;
+            W0 += r4.z;
+            W1 += r4.w;
+            W2 += w2;
         }
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const float Sx = fmaf(xc, S0[k], S1[k]);
+            v[0] += fmaf(xc, fmaf(xc, S0[k], 2.f * S1[k]), S2[k]);
+            v[1] = fmaf(yk[k], Sx, v[1]);
+            v[2] = fmaf(yk[k] * yk[k], S0[k], v[2]);
+            v[3] += Sx;
+            v[4] = fmaf(yk[k], S0[k], v[4]);
+            v[7] += S0[k];
+        }
+        v[5] = W0;
+        v[6] = W1;
+        v[8] = W2;
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-#pragma unroll
-        for (int o = RED_ROWS; o < 32; o <<= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 8);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
     }
     if (q == 0 && e < ns) {
         float* dst = sG[R.slot[e]];
@@ -170,67 +191,71 @@ __device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, const float
     }
 }
 
-// The adjoint of one tile (every thread of the CTA calls it with the same
-// tile; the shared arrays are the calling kernel's, one set per CTA).
-template <int TW, int TH>
-__device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, uint32_t tile) {
-    __shared__ float4 sV[BWD_BATCH];
-    __shared__ float2 sDE[BWD_BATCH];
-    __shared__ float4 sC[BWD_BATCH];
-    __shared__ uint8_t sM[BWD_BATCH];
-    __shared__ uint8_t sL[8][BWD_BATCH];
-    __shared__ uint32_t sId[BWD_BATCH];
-    __shared__ float sG[BWD_BATCH][9];
-    __shared__ uint32_t sLast[8];
-    __shared__ BwdRed sR[8];
-    __shared__ float4 sGp[256];   // (dL/drgb of the thread's pixel, 0)
-    static_assert(TW % 8 == 0, "row groups of 8 pixels");
+// The adjoint of one tile in a warp-block layout (see Layout): every thread of
+// the CTA calls it with the same tile. Per lane, PPL pixels; their per-pixel
+// arithmetic runs packed two-wide when PPL = 2.
+template <int TW, int TH, int WX, int WY>
+__device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, uint32_t tile,
+                                         BwdSmem<Layout<TW, TH, WX, WY>::NW>& S) {
+    using Lay = Layout<TW, TH, WX, WY>;
+    constexpr int PPL = Lay::PPL, NT = Lay::NT, NW = Lay::NW;
+    using P = Px<PPL>;
     const int view = view_of_tile(vs, tile);
     const ViewRec& c = vs.v[view];
     const uint32_t lt = tile - c.tile_off;
     const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = lane % TW, ly = warp * (TH / 8) + lane / TW;
-    const int px = X0 + lx, py = Y0 + ly;
-    const bool inside = px < c.W && py < c.H;
     const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
-    const float xl = (float)lx - 0.5f * (TW - 1), yl = (float)ly - 0.5f * (TH - 1);
-    const float bx2 = xl * xl, bxy = xl * yl, by2 = yl * yl;
+    const int lx = (warp % Lay::NBX) * WX + lane % WX;
     uint2 r = p.ranges[tile];
     if (!LGS_CHECK(r.x <= r.y && (r.y == r.x || (int64_t)r.y <= p.status[LGS_ST_NUM_INSTANCES]), 21, p.status))
         r.y = r.x;
 
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, tail = 0.f;
-    uint32_t last = 0;
-    if (inside) {
-        const int64_t plane = (int64_t)c.W * c.H;
-        const int64_t pix = (int64_t)py * c.W + px;
-        const float* gr = p.dL_drgb + 3 * (int64_t)c.pix_off;
-        g0 = gr[pix];
-        g1 = gr[plane + pix];
-        g2 = gr[2 * plane + pix];
-        T = p.final_T[c.pix_off + pix];
-        last = p.n_contrib[c.pix_off + pix];
-        const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
-        tail = T * (c.bg[0] * g0 + c.bg[1] * g1 + c.bg[2] * g2 + gT);
+    P bx2, bxy, by2, bxl, byl, T, g0, g1, g2, tail, Ag;
+    uint32_t last[PPL];
+    uint32_t mylast = 0;
+    const int64_t plane = (int64_t)c.W * c.H;
+    const float* gr = p.dL_drgb + 3 * (int64_t)c.pix_off;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int ly = (warp / Lay::NBX) * WY + lane / WX + k * (WY / 2);
+        const int px = X0 + lx, py = Y0 + ly;
+        const float xl = (float)lx - 0.5f * (TW - 1), yl = (float)ly - 0.5f * (TH - 1);
+        bx2[k] = xl * xl;
+        bxy[k] = xl * yl;
+        by2[k] = yl * yl;
+        bxl[k] = xl;
+        byl[k] = yl;
+        T[k] = 1.f;
+        g0[k] = g1[k] = g2[k] = tail[k] = Ag[k] = 0.f;
+        last[k] = 0;
+        if (px < c.W && py < c.H) {
+            const int64_t pix = (int64_t)py * c.W + px;
+            g0[k] = gr[pix];
+            g1[k] = gr[plane + pix];
+            g2[k] = gr[2 * plane + pix];
+            T[k] = p.final_T[c.pix_off + pix];
+            last[k] = p.n_contrib[c.pix_off + pix];
+            const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
+            tail[k] = T[k] * (c.bg[0] * g0[k] + c.bg[1] * g1[k] + c.bg[2] * g2[k] + gT);
+        }
+        mylast = max(mylast, last[k]);
     }
-    sGp[threadIdx.x] = make_float4(g0, g1, g2, 0.f);
-    BwdRed& R = sR[warp];
-    float Ag = 0.f;   // <A, g>: the colour behind the current Gaussian, projected on g
-    uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
-    if (lane == 0) sLast[warp] = wlast;
+    BwdRed& R = S.red[warp];
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0) S.sLast[warp] = wlast;
     __syncthreads();
     uint32_t tlast = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) tlast = max(tlast, sLast[w]);
+    for (int w = 0; w < NW; ++w) tlast = max(tlast, S.sLast[w]);
     if (!LGS_CHECK(tlast <= r.y - r.x, 22, p.status)) tlast = r.y - r.x;
 
     for (int end = (int)tlast; end > 0; end -= BWD_BATCH) {
         const int begin = max(0, end - BWD_BATCH);
         const int nb = end - begin;
         __syncthreads();
-        if ((int)threadIdx.x < nb) {
-            const uint32_t pos = (uint32_t)(begin + threadIdx.x);
+        for (int sl = threadIdx.x; sl < nb; sl += NT) {
+            const uint32_t pos = (uint32_t)(begin + sl);
             const uint32_t id = p.vals[r.x + pos];
             const float4 xy = p.xy[id];
             const float4 co = p.conic[id];
@@ -240,25 +265,25 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             const float Dn = fmaf(co.x, dx, co.y * dy);
             const float En = fmaf(co.y, dx, co.z * dy);
             const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
-            sV[threadIdx.x] = make_float4(-0.5f * LOG2E_B * co.x, -LOG2E_B * co.y, -0.5f * LOG2E_B * co.z,
-                                          fmaf(Fn, LOG2E_B, __log2f(co.w)));
-            sDE[threadIdx.x] = make_float2(Dn * LOG2E_B, En * LOG2E_B);
-            sC[threadIdx.x] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
-            sM[threadIdx.x] = (uint8_t)warp_mask<TW, TH>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
+            S.sV[sl] = make_float4(-0.5f * LOG2E_B * co.x, -LOG2E_B * co.y, -0.5f * LOG2E_B * co.z,
+                                   fmaf(Fn, LOG2E_B, __log2f(co.w)));
+            S.sDE[sl] = make_float2(Dn * LOG2E_B, En * LOG2E_B);
+            S.sC[sl] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
+            S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                            __fadd_rn(xy.y, xy.w), X0, Y0);
-            sId[threadIdx.x] = id;
+            S.sId[sl] = id;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) sG[threadIdx.x][k] = 0.f;
+            for (int k = 0; k < 9; ++k) S.sG[sl][k] = 0.f;
         }
         __syncthreads();
         if (wlast > (uint32_t)begin) {
             // the warp's list of the batch (set mask bits up to its last
             // contributor), compacted in order and walked back to front
-            uint8_t* sLw = sL[warp];
+            uint8_t* sLw = S.sL[warp];
             int nl = 0;
             for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
-                const bool hit = jj < nb && ((sM[jj] >> warp) & 1u) && (uint32_t)(begin + jj) < wlast;
+                const bool hit = jj < nb && ((S.sM[jj] >> warp) & 1u) && (uint32_t)(begin + jj) < wlast;
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                 if (hit) sLw[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
                 nl += __popc(bal);
@@ -268,52 +293,76 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
 #pragma unroll 1
             for (int i = nl - 1; i >= 0; --i) {
                 const int g = sLw[i];
-                const float4 V = sV[g];
-                const float2 DE = sDE[g];
-                const float4 col = sC[g];
+                const float4 V = S.sV[g];
+                const float2 DE = S.sDE[g];
+                const float4 col = S.sC[g];
                 const uint32_t pos = __float_as_uint(col.w);
-                const float pw = fmaf(V.x, bx2, fmaf(V.y, bxy, fmaf(V.z, by2,
-                                 fmaf(DE.x, xl, fmaf(DE.y, yl, V.w)))));
-                const bool contrib = pos <= last && pw >= LOG2_ALPHA_MIN_B;
-                if (!__any_sync(0xffffffffu, contrib)) continue;   // nothing to reduce
-                const float e2 = ex2_approx_b(pw);
-                const float al = fminf(0.99f, e2);
-                // branch-free: lanes that do not contribute get alpha 0, which
-                // leaves T and the accumulated colour exactly as they were
-                const float inv = __fdividef(1.f, 1.f - al);   // 1 - alpha >= 0.01
-                const float Tk = T * inv;
-                const float ac = contrib ? al : 0.f;
-                const float w = ac * Tk;
+                const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
+                             pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
+                bool contrib[PPL];
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    contrib[k] = pos <= last[k] && pw[k] >= LOG2_ALPHA_MIN_B;
+                    any = any || contrib[k];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;   // nothing to reduce
+                // branch-free: pixels that do not contribute get alpha 0, which
+                // leaves T and the colour behind exactly as they were
+                P e2, al, inv, ac;
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    e2[k] = ex2_approx_b(pw[k]);
+                    al[k] = fminf(0.99f, e2[k]);
+                    inv[k] = __fdividef(1.f, 1.f - al[k]);   // 1 - alpha >= 0.01
+                    ac[k] = contrib[k] ? al[k] : 0.f;
+                }
+                const P Tk = pmul(T, inv);
+                const P w = pmul(ac, Tk);
                 // <rgb_k - A_k, g>, and A <- alpha rgb + (1 - alpha) A carried as <A, g>
-                const float cg = fmaf(col.z, g2, fmaf(col.y, g1, col.x * g0)) - Ag;
-                const float dal = Tk * cg - tail * inv;
-                Ag = fmaf(ac, cg, Ag);
-                T = contrib ? Tk : T;
-                const float dp = (contrib && !(e2 > 0.99f)) ? dal * al : 0.f;
-                const int cc = red_col(ns, lane);
-                R.dp[ns][cc] = dp;
-                R.w[ns][cc] = w;
+                const P cg = padd(pfma(bcast<PPL>(col.z), g2, pfma(bcast<PPL>(col.y), g1,
+                                                                   pmul(bcast<PPL>(col.x), g0))),
+                                  pneg(Ag));
+                const P dal = pfma(Tk, cg, pneg(pmul(tail, inv)));
+                Ag = pfma(ac, cg, Ag);
+                const P dal_al = pmul(dal, al);
+                float dp[2] = {0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    T[k] = contrib[k] ? Tk[k] : T[k];
+                    dp[k] = (contrib[k] && !(e2[k] > 0.99f)) ? dal_al[k] : 0.f;
+                }
+                // the lane's colour sums over its pixels
+                const P wg0 = pmul(w, g0), wg1 = pmul(w, g1), wg2 = pmul(w, g2);
+                float W0 = wg0[0], W1 = wg1[0], W2 = wg2[0];
+                if (PPL == 2) {
+                    W0 += wg0[PPL - 1];
+                    W1 += wg1[PPL - 1];
+                    W2 += wg2[PPL - 1];
+                }
+                const int cc = lane ^ (ns & 7);
+                R.R4[ns][cc] = make_float4(dp[0], dp[1], W0, W1);
+                R.R1[ns][cc] = W2;
                 if (lane == 0) R.slot[ns] = (uint32_t)g;
                 if (++ns == RED_ROWS) {
                     __syncwarp();
-                    reduce_rows<TW, TH>(R, ns, sGp + 32 * warp, sG, lane, warp);
+                    reduce_rows<TW, TH, WX, WY>(R, ns, S.sG, lane, warp);
                     __syncwarp();
                     ns = 0;
                 }
             }
             if (ns > 0) {
                 __syncwarp();
-                reduce_rows<TW, TH>(R, ns, sGp + 32 * warp, sG, lane, warp);
+                reduce_rows<TW, TH, WX, WY>(R, ns, S.sG, lane, warp);
                 __syncwarp();
             }
         }
         __syncthreads();
-        if ((int)threadIdx.x < nb) {
+        for (int t = threadIdx.x; t < nb; t += NT) {
             // hoisted gradients (A, B, C, D, E, F in natural-log units) -> (a, b, c, ln o, Dx, Dy)
-            const int t = threadIdx.x;
-            const float gA = sG[t][0], gB = sG[t][1], gC = sG[t][2], gD = sG[t][3], gE = sG[t][4];
-            const float gF = sG[t][7];
-            const uint32_t id = sId[t];
+            const float gA = S.sG[t][0], gB = S.sG[t][1], gC = S.sG[t][2], gD = S.sG[t][3], gE = S.sG[t][4];
+            const float gF = S.sG[t][7];
+            const uint32_t id = S.sId[t];
             const float4 xy = p.xy[id];
             const float4 co = p.conic[id];
             const float dx = __fadd_rn(xy.x - Ox, xy.z);
@@ -332,7 +381,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                 atomicAdd(reinterpret_cast<float4*>(p.g_conic) + id, make_float4(ga, gbb, gc, go));
                 atomicAdd(reinterpret_cast<float2*>(p.g_xy) + id, make_float2(gdx, gdy));
             }
-            const float gr0 = sG[t][5], gr1 = sG[t][6], gr2 = sG[t][8];
+            const float gr0 = S.sG[t][5], gr1 = S.sG[t][6], gr2 = S.sG[t][8];
             if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
                 atomicAdd(reinterpret_cast<float4*>(p.g_rgb) + id, make_float4(gr0, gr1, gr2, 0.f));
             }
@@ -340,16 +389,21 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
     }
 }
 
-// One CTA per tile.
-template <int TW, int TH>
-__global__ void __launch_bounds__(256, 5) render_bwd_localgs(BwdParams p, Views vs) {
-    bwd_tile<TW, TH>(p, vs, blockIdx.x);
+// One CTA per tile (shared memory: the dynamic allocation of the launch).
+template <int TW, int TH, int WX, int WY>
+__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_bwd_localgs(BwdParams p, Views vs) {
+    extern __shared__ __align__(16) unsigned char bwd_smem[];
+    auto& S = *reinterpret_cast<BwdSmem<Layout<TW, TH, WX, WY>::NW>*>(bwd_smem);
+    bwd_tile<TW, TH, WX, WY>(p, vs, blockIdx.x, S);
 }
 
 // Persistent CTAs: each pulls the next tile index from the work-queue counter
 // LGS_ST_QUEUE_BWD (zeroed by the launcher) until all tiles are taken.
-template <int TW, int TH>
-__global__ void __launch_bounds__(256, 5) render_bwd_localgs_persistent(BwdParams p, Views vs) {
+template <int TW, int TH, int WX, int WY>
+__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_bwd_localgs_persistent(BwdParams p,
+                                                                                         Views vs) {
+    extern __shared__ __align__(16) unsigned char bwd_smem[];
+    auto& S = *reinterpret_cast<BwdSmem<Layout<TW, TH, WX, WY>::NW>*>(bwd_smem);
     __shared__ uint32_t s_tile;
     unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE_BWD);
     for (;;) {
@@ -358,7 +412,7 @@ __global__ void __launch_bounds__(256, 5) render_bwd_localgs_persistent(BwdParam
         const uint32_t tile = s_tile;
         __syncthreads();
         if (tile >= vs.n_tiles) break;
-        bwd_tile<TW, TH>(p, vs, tile);
+        bwd_tile<TW, TH, WX, WY>(p, vs, tile, S);
         __syncthreads();
     }
 }
@@ -724,23 +778,44 @@ __global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) 
     for (int k = 0; k < NK * 3; ++k) dsp[k] += dsh[k];
 }
 
+template <int TW, int TH, int WX, int WY>
+lgs_status launch_bwd_layout(const BwdParams& bp, const Views& vs, bool persistent, cudaStream_t s) {
+    using Lay = Layout<TW, TH, WX, WY>;
+    const int smem = (int)sizeof(BwdSmem<Lay::NW>);
+    if (!persistent) {
+        auto k = render_bwd_localgs<TW, TH, WX, WY>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return LGS_ERR_CUDA;
+        k<<<vs.n_tiles, Lay::NT, smem, s>>>(bp, vs);
+        return cuda_status(cudaGetLastError());
+    }
+    auto k = render_bwd_localgs_persistent<TW, TH, WX, WY>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return LGS_ERR_CUDA;
+    if (cudaMemsetAsync(bp.status + LGS_ST_QUEUE_BWD, 0, sizeof(int64_t), s) != cudaSuccess)
+        return LGS_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Lay::NT, smem);
+    const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+    k<<<g, Lay::NT, smem, s>>>(bp, vs);
+    return cuda_status(cudaGetLastError());
+}
+
 template <int TW, int TH>
-lgs_status launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, bool persistent, cudaStream_t s) {
+lgs_status launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, int wx, int wy, bool persistent,
+                             cudaStream_t s) {
     if (mode == LGS_MODE_PLAIN) {
         render_bwd_plain<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
-    } else if (!persistent) {
-        render_bwd_localgs<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
-    } else {
-        if (cudaMemsetAsync(bp.status + LGS_ST_QUEUE_BWD, 0, sizeof(int64_t), s) != cudaSuccess)
-            return LGS_ERR_CUDA;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_localgs_persistent<TW, TH>, 256, 0);
-        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
-        render_bwd_localgs_persistent<TW, TH><<<g, 256, 0, s>>>(bp, vs);
+        return cuda_status(cudaGetLastError());
     }
-    return cuda_status(cudaGetLastError());
+    if (wx == TW && wy == TH / 8) return launch_bwd_layout<TW, TH, TW, TH / 8>(bp, vs, persistent, s);
+    if constexpr (TW == 16) {
+        if (wx == 8 && wy == 4) return launch_bwd_layout<16, 16, 8, 4>(bp, vs, persistent, s);
+        if (wx == 16 && wy == 4) return launch_bwd_layout<16, 16, 16, 4>(bp, vs, persistent, s);
+    }
+    return launch_bwd_layout<TW, TH, 8, 8>(bp, vs, persistent, s);
 }
 
 }  // namespace lgs
@@ -794,9 +869,12 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
     const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
     if (persistent && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
-    if (cfg->tile_w == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, persistent, s);
-    else if (cfg->tile_w == 8) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, persistent, s);
-    else st = launch_render_bwd<32, 8>(bp, vs, cfg->mode, persistent, s);
+    int wx = 0, wy = 0;
+    if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
+    if (cfg->mode != LGS_MODE_LOCALGS && (wx != cfg->tile_w || wy != cfg->tile_h / 8)) return LGS_ERR_UNSUPPORTED;
+    if (cfg->tile_w == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else if (cfg->tile_w == 8) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else st = launch_render_bwd<32, 8>(bp, vs, cfg->mode, wx, wy, persistent, s);
     if (st != LGS_OK) return st;
     PreBwdParams pp;
     pp.means = g->means; pp.scales = g->scales; pp.quats = g->quats; pp.sh = g->sh; pp.n = g->n;

@@ -281,4 +281,46 @@ __device__ __forceinline__ uint32_t warp_mask(float a, float b, float c, float o
     return block_mask<TW, TH, TW, TH / 8>(a, b, c, o, mux, muy, X0, Y0);
 }
 
+// ---------------------------------------------------------------- warp layouts
+// Warp layout of a Local-GS tile: NW = (TW/WX) * (TH/WY) warps, warp w owning
+// the WX x WY pixel block (w % (TW/WX), w / (TW/WX)) and bit w of the block
+// mask. Lane l evaluates pixel (l % WX, l / WX) of its block; with 64-pixel
+// blocks (PPL = 2 pixels per lane) also the pixel WY/2 rows below, and the
+// per-pixel FP32 arithmetic of the pair runs as packed two-wide instructions
+// (fma.rn.f32x2 / mul.rn.f32x2), one issue slot for both pixels. The paper's
+// layout is WX = TW, WY = TH/8 (eight full-width strips, one pixel per lane).
+template <int TW, int TH, int WX, int WY>
+struct Layout {
+    static constexpr int NBX = TW / WX, NBY = TH / WY, NW = NBX * NBY, NT = 32 * NW;
+    static constexpr int PPL = WX * WY / 32;
+    static_assert(TW % WX == 0 && TH % WY == 0, "blocks tile the tile");
+    static_assert(PPL == 1 || PPL == 2, "one or two pixels per lane");
+    static_assert(NW == 4 || NW == 8, "4 or 8 warps per tile");
+    static_assert(32 % WX == 0 || WX == 32, "a warp row is whole lanes");
+};
+
+// P pixels' worth of one float, with the packed FP32 operations on two.
+template <int P> struct Px;
+template <> struct Px<1> {
+    float v;
+    __device__ __forceinline__ float& operator[](int) { return v; }
+    __device__ __forceinline__ float operator[](int) const { return v; }
+};
+template <> struct Px<2> {
+    float2 v;
+    __device__ __forceinline__ float& operator[](int k) { return k ? v.y : v.x; }
+    __device__ __forceinline__ float operator[](int k) const { return k ? v.y : v.x; }
+};
+__device__ __forceinline__ Px<1> pfma(Px<1> a, Px<1> b, Px<1> c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Px<2> pfma(Px<2> a, Px<2> b, Px<2> c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Px<1> pmul(Px<1> a, Px<1> b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<2> pmul(Px<2> a, Px<2> b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<1> padd(Px<1> a, Px<1> b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<2> padd(Px<2> a, Px<2> b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Px<1> pneg(Px<1> a) { return {-a.v}; }
+__device__ __forceinline__ Px<2> pneg(Px<2> a) { return {make_float2(-a.v.x, -a.v.y)}; }
+template <int P> __device__ __forceinline__ Px<P> bcast(float s);
+template <> __device__ __forceinline__ Px<1> bcast<1>(float s) { return {s}; }
+template <> __device__ __forceinline__ Px<2> bcast<2>(float s) { return {make_float2(s, s)}; }
+
 }  // namespace lgs

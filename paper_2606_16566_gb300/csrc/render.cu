@@ -100,51 +100,12 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 }
 
 // ------------------------------------------------------------------ Local-GS
-// Warp layout of a Local-GS tile: NW = (TW/WX) * (TH/WY) warps, warp w owning
-// the WX x WY pixel block (w % (TW/WX), w / (TW/WX)) and bit w of the block
-// mask. Lane l evaluates pixel (l % WX, l / WX) of its block; with 64-pixel
-// blocks (PPL = 2 pixels per lane) also the pixel WY/2 rows below, and the
-// per-pixel FP32 arithmetic of the pair runs as packed two-wide instructions
-// (fma.rn.f32x2 / mul.rn.f32x2), one issue slot for both pixels. The paper's
-// layout is WX = TW, WY = TH/8 (eight full-width strips, one pixel per lane).
-template <int TW, int TH, int WX, int WY>
-struct Layout {
-    static constexpr int NBX = TW / WX, NBY = TH / WY, NW = NBX * NBY, NT = 32 * NW;
-    static constexpr int PPL = WX * WY / 32;
-    static_assert(TW % WX == 0 && TH % WY == 0, "blocks tile the tile");
-    static_assert(PPL == 1 || PPL == 2, "one or two pixels per lane");
-    static_assert(NW == 4 || NW == 8, "4 or 8 warps per tile");
-    static_assert(32 % WX == 0 || WX == 32, "a warp row is whole lanes");
-};
-
-// P pixels' worth of one float, with the packed FP32 operations on two.
-template <int P> struct Px;
-template <> struct Px<1> {
-    float v;
-    __device__ __forceinline__ float& operator[](int) { return v; }
-    __device__ __forceinline__ float operator[](int) const { return v; }
-};
-template <> struct Px<2> {
-    float2 v;
-    __device__ __forceinline__ float& operator[](int k) { return k ? v.y : v.x; }
-    __device__ __forceinline__ float operator[](int k) const { return k ? v.y : v.x; }
-};
-__device__ __forceinline__ Px<1> pfma(Px<1> a, Px<1> b, Px<1> c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ Px<2> pfma(Px<2> a, Px<2> b, Px<2> c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ Px<1> pmul(Px<1> a, Px<1> b) { return {__fmul_rn(a.v, b.v)}; }
-__device__ __forceinline__ Px<2> pmul(Px<2> a, Px<2> b) { return {__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ Px<1> padd(Px<1> a, Px<1> b) { return {__fadd_rn(a.v, b.v)}; }
-__device__ __forceinline__ Px<2> padd(Px<2> a, Px<2> b) { return {__fadd2_rn(a.v, b.v)}; }
-template <int P> __device__ __forceinline__ Px<P> bcast(float s);
-template <> __device__ __forceinline__ Px<1> bcast<1>(float s) { return {s}; }
-template <> __device__ __forceinline__ Px<2> bcast<2>(float s) { return {make_float2(s, s)}; }
-
 template <int NB>
 struct LocalSmem {
     float4 raw[2][3][NB];  // double-buffered cp.async landing zone: xy, conic, rgb records
     float4 sV[NB];         // (A, B, C, F), log2 domain
     float2 sDE[NB];        // (D, E)
-    float4 sC[NB];         // (-r, -g, -b, -): colour negated, see the blend
+    float4 sC[NB];         // (-r, -g, -b, clamp flag): colour negated, see the blend
     uint8_t sM[NB];        // warp-block mask
     uint8_t sL[8][NB];     // per warp: batch indices of its set mask bits, in order
 };
@@ -272,7 +233,10 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 S.sV[sl] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
                                        fmaf(Fn, LOG2E, __log2f(co.w)));
                 S.sDE[sl] = make_float2(Dn * LOG2E, En * LOG2E);
-                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, 0.f);
+                // w: 1 when the 0.99 clamp can act (o > 0.9). With o <= 0.9,
+                // 2^pw stays below 0.91 even with the FP32 rounding of the
+                // hoisted exponent, so the clamp is the identity there
+                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, co.w > 0.9f ? 1.f : 0.f);
                 S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                                __fadd_rn(xy.y, xy.w), X0, Y0);
             }
@@ -316,7 +280,11 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                     // updates below need no separate negation
                     P nal;
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, -ex2_approx(pw[k]));
+                    for (int k = 0; k < PPL; ++k) nal[k] = -ex2_approx(pw[k]);
+                    if (ncol.w != 0.f) {                     // warp-uniform
+#pragma unroll
+                        for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, nal[k]);
+                    }
                     if (VAR == VAR_LITERAL) {
                         const P nw = pmul(nal, T);          // -w = -alpha T
                         C0 = pfma(bcast<PPL>(ncol.x), nw, C0);

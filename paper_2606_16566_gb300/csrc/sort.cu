@@ -168,10 +168,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* t
 // cooperatively: lane l produces instances l, l+32, ... of the range, finds
 // the owning entry by a binary search over the warp's inclusive prefix counts
 // (shuffles), and the stores of a warp land on consecutive addresses.
+template <typename KT>
 __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const uint32_t* tiles,
                                                   const uint32_t* offsets, const uint64_t* rect,
                                                   int64_t m, int64_t n, int64_t* status,
-                                                  int64_t capacity, Views vs, uint32_t* tkey,
+                                                  int64_t capacity, Views vs, KT* tkey,
                                                   uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256) emit_pairs(const uint32_t* order, const u
                 const uint32_t tile = otoff + (oy0 + ry) * ogx + ox0 + rx;
                 if (LGS_CHECK((int64_t)start + e < capacity, 1, status) &&
                     LGS_CHECK(tile < vs.n_tiles, 2, status) && LGS_CHECK(oent < (uint64_t)m, 3, status)) {
-                    tkey[start + e] = tile;
+                    tkey[start + e] = (KT)tile;
                     tval[start + e] = oent;
                 }
             }
@@ -413,11 +414,11 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
 // lengths). Should the recount ever differ from count_tight's (it cannot: same
 // function, same inputs), the warp writes only inside its own range, pads it
 // with tile 0 / entry 0 and records LGS_ERR_INTERNAL.
-template <int TW, int TH>
+template <int TW, int TH, typename KT>
 __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, const uint32_t* tiles_sorted,
                                                         const uint32_t* offsets, const uint4* rec,
                                                         int64_t m, int64_t n, int64_t* status,
-                                                        int64_t capacity, Views vs, uint32_t* tkey,
+                                                        int64_t capacity, Views vs, KT* tkey,
                                                         uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
                 const uint32_t tile = otoff + ((uint32_t)rlo + r) * ogx + tx;
                 if (q < total && LGS_CHECK((int64_t)start + q < capacity, 4, status) &&
                     LGS_CHECK(tile < vs.n_tiles, 5, status) && LGS_CHECK(oent < (uint64_t)m, 6, status)) {
-                    tkey[start + q] = tile;
+                    tkey[start + q] = (KT)tile;
                     tval[start + q] = oent;
                 }
             }
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
         }
         if (run != total) {
             for (uint32_t q = run + lane; q < total; q += 32) {
-                tkey[start + q] = 0u;
+                tkey[start + q] = (KT)0;
                 tval[start + q] = 0u;
             }
             if (lane == 0) report_error(status, LGS_ERR_INTERNAL, (int64_t)total - (int64_t)run);
@@ -572,38 +573,49 @@ __global__ void __launch_bounds__(256) onesweep_histogram(OsSrc src, const int64
 // one private histogram per warp, and a warp-uniform fast path -- when all 128
 // digits a warp loads at once are equal (instances of neighbouring Gaussians
 // mostly share the high tile-id byte) one atomic adds them all.
-__global__ void __launch_bounds__(256) key_histogram(const uint32_t* keys, const int64_t* cnt,
+template <typename KT>
+__global__ void __launch_bounds__(256) key_histogram(const KT* keys, const int64_t* cnt,
                                                      int64_t count, int npass, uint32_t* ghist) {
+    constexpr int PER = 16 / sizeof(KT);        // keys per 16-B load
     __shared__ uint32_t h[8][OS_MAX_DIGITS][RADIX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 8 * OS_MAX_DIGITS * RADIX; i += blockDim.x) (&h[0][0][0])[i] = 0;
     __syncthreads();
     const int64_t K = pass_count(cnt, count);
-    const int64_t n4 = K / 4;
+    const int64_t n4 = K / PER;
     const uint4* k4 = reinterpret_cast<const uint4*>(keys);
     for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < n4; base += (int64_t)gridDim.x * 256) {
         const int64_t q = base + lane;
         const bool ok = q < n4;
-        const uint4 v = ok ? k4[q] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 v4 = ok ? k4[q] : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t kv[PER];
+        if constexpr (PER == 4) {
+            kv[0] = v4.x; kv[1] = v4.y; kv[2] = v4.z; kv[3] = v4.w;
+        } else {
+            const uint32_t w4[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                kv[2 * r] = w4[r] & 0xffffu;
+                kv[2 * r + 1] = w4[r] >> 16;
+            }
+        }
         const int nok = __popc(__ballot_sync(0xffffffffu, ok));
         for (int p = 0; p < npass; ++p) {
             const int sh = 8 * p;
-            const uint32_t d0 = (v.x >> sh) & 0xffu, d1 = (v.y >> sh) & 0xffu;
-            const uint32_t d2 = (v.z >> sh) & 0xffu, d3 = (v.w >> sh) & 0xffu;
-            const uint32_t first = __shfl_sync(0xffffffffu, d0, 0);
-            const bool uni = !ok || (d0 == first && d1 == first && d2 == first && d3 == first);
-            if (__all_sync(0xffffffffu, uni)) {
-                if (lane == 0) atomicAdd(&h[warp][p][first], 4u * (uint32_t)nok);
+            const uint32_t first = __shfl_sync(0xffffffffu, (kv[0] >> sh) & 0xffu, 0);
+            bool uni = true;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) uni = uni && ((kv[r] >> sh) & 0xffu) == first;
+            if (__all_sync(0xffffffffu, !ok || uni)) {
+                if (lane == 0) atomicAdd(&h[warp][p][first], (uint32_t)PER * (uint32_t)nok);
             } else if (ok) {
-                atomicAdd(&h[warp][p][d0], 1u);
-                atomicAdd(&h[warp][p][d1], 1u);
-                atomicAdd(&h[warp][p][d2], 1u);
-                atomicAdd(&h[warp][p][d3], 1u);
+#pragma unroll
+                for (int r = 0; r < PER; ++r) atomicAdd(&h[warp][p][(kv[r] >> sh) & 0xffu], 1u);
             }
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x < (int)(K - 4 * n4)) {       // the K mod 4 tail
-        const uint32_t k = keys[4 * n4 + threadIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x < (int)(K - PER * n4)) {       // the K mod PER tail
+        const uint32_t k = keys[PER * n4 + threadIdx.x];
         for (int p = 0; p < npass; ++p) atomicAdd(&h[0][p][(k >> (8 * p)) & 0xffu], 1u);
     }
     __syncthreads();
@@ -942,29 +954,36 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
 // ------------------------------------------------------------------ ranges
 // Per-tile [start, end) of the sorted tile ids; each thread takes 4
 // consecutive instances (one 16-B load when all 4 lie below K).
-__global__ void __launch_bounds__(256) tile_ranges(const uint32_t* tkey, int64_t* status,
+template <typename KT>
+__global__ void __launch_bounds__(256) tile_ranges(const KT* tkey, int64_t* status,
                                                    int64_t capacity, uint32_t n_tiles, uint2* ranges) {
+    constexpr int PER = 16 / sizeof(KT);        // ids per 16-B load
     const int64_t K = sort_count(status, capacity);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * q < K;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; PER * q < K;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i0 = 4 * q;
-        uint32_t t[4];
-        if (i0 + 3 < K) {
+        const int64_t i0 = PER * q;
+        uint32_t t[PER];
+        if (i0 + PER - 1 < K) {
             const uint4 v = reinterpret_cast<const uint4*>(tkey)[q];
-            t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                if constexpr (PER == 4) t[r] = w4[r];
+                else t[r] = (w4[r / 2] >> (16 * (r & 1))) & 0xffffu;
+            }
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) t[r] = i0 + r < K ? tkey[i0 + r] : 0u;
+            for (int r = 0; r < PER; ++r) t[r] = i0 + r < K ? (uint32_t)tkey[i0 + r] : 0u;
         }
-        uint32_t prev = i0 > 0 ? tkey[i0 - 1] : 0xffffffffu;
+        uint32_t prev = i0 > 0 ? (uint32_t)tkey[i0 - 1] : 0xffffffffu;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < PER; ++r) {
             const int64_t i = i0 + r;
             if (i >= K) break;
             if (!LGS_CHECK(t[r] < n_tiles, 8, status)) break;
             if (i == 0 || prev != t[r]) ranges[t[r]].x = (uint32_t)i;
-            const uint32_t next = r < 3 ? (i + 1 < K ? t[r + 1] : 0xffffffffu)
-                                        : (i + 1 < K ? tkey[i + 1] : 0xffffffffu);
+            const uint32_t next = r < PER - 1 ? (i + 1 < K ? t[r + 1] : 0xffffffffu)
+                                              : (i + 1 < K ? (uint32_t)tkey[i + 1] : 0xffffffffu);
             if (i == K - 1 || next != t[r]) ranges[t[r]].y = (uint32_t)(i + 1);
             prev = t[r];
         }
@@ -981,7 +1000,8 @@ __global__ void gather_tiles(const uint32_t* order, const uint32_t* tiles, int64
 }
 
 // Optional 64-bit keys of the sorted instances: (tile << 32) | bits(depth).
-__global__ void write_keys(const uint32_t* tkey, const uint32_t* vals, const float* depth,
+template <typename KT>
+__global__ void write_keys(const KT* tkey, const uint32_t* vals, const float* depth,
                            const int64_t* status, int64_t capacity, uint64_t* keys) {
     const int64_t K = sort_count(status, capacity);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
@@ -1126,6 +1146,76 @@ extern "C" size_t lgs_sort_workspace_size(int64_t m, int64_t capacity) {
     return sort_ws_layout(m, capacity, nullptr, nullptr);
 }
 
+struct SortTileArgs {
+    const uint32_t* order;
+    const lgs_pre_out* pre;
+    int64_t n, m;
+    const Views* vs;
+    int64_t capacity;
+    uint64_t* keys;
+    uint32_t* vals;
+    uint32_t* ranges;
+    const SortWs* ws;
+    int64_t* d_status;
+    bool tight, onesweep;
+};
+
+// Emission of the (tile id, entry) pairs in depth order, the stable LSD
+// passes over the tile-id bits, the tile ranges and (if asked for) the 64-bit
+// keys, with tile ids of type KT (u16 when every id fits).
+template <typename KT>
+static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
+    const Views* vs = a.vs;
+    const SortWs* ws = a.ws;
+    const int64_t m = a.m, capacity = a.capacity;
+    const unsigned eg = (unsigned)ceil_div(m, 256);
+    // the value buffers alternate so that the last pass lands in vals
+    const int passes = tile_passes(vs->n_tiles);
+    KT *ka = reinterpret_cast<KT*>(ws->ak), *kb = reinterpret_cast<KT*>(ws->bk);
+    uint32_t *va = (passes & 1) ? ws->bv : a.vals, *vb = (passes & 1) ? a.vals : ws->bv;
+    if (a.tight) {
+        if (vs->tile_w == 16)
+            emit_pairs_tight<16, 16, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
+                                                            m, a.n, a.d_status, capacity, *vs, ka, va);
+        else if (vs->tile_w == 8)
+            emit_pairs_tight<8, 32, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
+                                                           m, a.n, a.d_status, capacity, *vs, ka, va);
+        else
+            emit_pairs_tight<32, 8, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
+                                                           m, a.n, a.d_status, capacity, *vs, ka, va);
+    } else {
+        emit_pairs<KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, a.pre->rect, m, a.n, a.d_status,
+                                          capacity, *vs, ka, va);
+    }
+    const int64_t* kcount = a.d_status + LGS_ST_NUM_INSTANCES;
+    uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
+    if (passes > 0) {
+        cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * passes, s);
+        key_histogram<KT><<<152 * 4, 256, 0, s>>>(ka, kcount, capacity, passes, tbases);
+        onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
+    }
+    for (int p = 0; p < passes; ++p) {
+        if constexpr (sizeof(KT) == 4) {
+            radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p, tbases + p * RADIX, ws,
+                       a.d_status, s, a.onesweep);
+        } else {
+            const int64_t nb = ceil_div(capacity, RS_TILE);
+            uint32_t* counts = reinterpret_cast<uint32_t*>(ws->look);
+            const RsSrc<KT> rs{ka, va, nullptr, nullptr};
+            rs_upsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kcount, capacity, 8 * p, counts, nb);
+            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, kcount, capacity, tbases + p * RADIX);
+            rs_downsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p, counts, nb,
+                                                                 a.d_status);
+        }
+        KT* t = ka; ka = kb; kb = t;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+    // ka holds the sorted tile ids, va == vals
+    uint2* r2 = reinterpret_cast<uint2*>(a.ranges);
+    tile_ranges<KT><<<152 * 4, 256, 0, s>>>(ka, a.d_status, capacity, vs->n_tiles, r2);
+    if (a.keys) write_keys<KT><<<152 * 8, 256, 0, s>>>(ka, a.vals, a.pre->depth, a.d_status, capacity, a.keys);
+}
+
 // Enqueues the full stage given a workspace layout (shared by the entry points):
 //  1. stable LSD sort of the visible entries by depth (the first pass drops
 //     the culled ones),
@@ -1183,42 +1273,11 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
     scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums,
                                                             ws->offsets);
-    // 3. emission; the value buffers alternate so that the last pass lands in vals
-    const int passes = tile_passes(vs->n_tiles);
-    uint32_t *ka = ws->ak, *kb = ws->bk;
-    uint32_t *va = (passes & 1) ? ws->bv : vals, *vb = (passes & 1) ? vals : ws->bv;
-    if (tight) {
-        if (vs->tile_w == 16)
-            emit_pairs_tight<16, 16><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
-                                                        m, n, d_status, capacity, *vs, ka, va);
-        else if (vs->tile_w == 8)
-            emit_pairs_tight<8, 32><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
-                                                       m, n, d_status, capacity, *vs, ka, va);
-        else
-            emit_pairs_tight<32, 8><<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, ws->erec,
-                                                       m, n, d_status, capacity, *vs, ka, va);
-    } else {
-        emit_pairs<<<eg, 256, 0, s>>>(order, ws->tiles_s, ws->offsets, pre->rect, m, n, d_status,
-                                      capacity, *vs, ka, va);
-    }
-    // 4. tile-id passes over the K instances
-    const int64_t* kcount = d_status + LGS_ST_NUM_INSTANCES;
-    uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
-    if (passes > 0) {
-        cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * passes, s);
-        key_histogram<<<152 * 4, 256, 0, s>>>(ka, kcount, capacity, passes, tbases);
-        onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
-    }
-    for (int p = 0; p < passes; ++p) {
-        radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p,
-                   tbases + p * RADIX, ws, d_status, s, os);
-        uint32_t* t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
-    }
-    // 5. ranges (ka holds the sorted tile ids, va == vals)
-    uint2* r2 = reinterpret_cast<uint2*>(ranges);
-    tile_ranges<<<152 * 4, 256, 0, s>>>(ka, d_status, capacity, vs->n_tiles, r2);
-    if (keys) write_keys<<<152 * 8, 256, 0, s>>>(ka, vals, pre->depth, d_status, capacity, keys);
+    // 3-5: emission, tile-id passes and ranges, with u16 tile ids when the
+    //      batch has at most 2^16 tiles (reduce-then-scan passes only)
+    const SortTileArgs ta{order, pre, n, m, vs, capacity, keys, vals, ranges, ws, d_status, tight, os};
+    if (!os && vs->n_tiles <= 65536u) tile_stage<uint16_t>(ta, s);
+    else tile_stage<uint32_t>(ta, s);
     return cuda_status(cudaGetLastError());
 }
 
