@@ -377,13 +377,16 @@ def _graph_ms(graph, flush, reps):
 def run_indoor(dev, steps):
     """The indoor training step: 2.8M SH3 Gaussians on room walls, one 1332x876
     view; forward, L1 loss against a seeded random target, full adjoint, all in
-    one CUDA graph (tight-box emission)."""
+    one CUDA graph (tight-box emission; tile shape, warp block and launch from
+    the autotuner on forward + backward)."""
     import torch
     from paper_2606_16566_gb300 import batch, lgs, scenes
     sc, cams = scenes.indoor()
     g = lgs.to_device(sc, dev)
     del sc
-    r = batch.Renderer(g, cams, backward=True, tight=True)
+    tune = batch.autotune(g, cams, backward=True, reps=3, use_cache=False, tight=True, batches=(256,))
+    r = batch.Renderer(g, cams, tile=tune["tile"], persistent=tune["persistent"], backward=True, tight=True,
+                       batch=tune["batch"], block=tune["block"])
     target = torch.rand(r.rgb.shape, generator=torch.Generator(device=dev).manual_seed(7), device=dev)
     diff = torch.empty_like(r.rgb)
     inv_n = 1.0 / r.rgb.numel()
@@ -412,13 +415,14 @@ def run_indoor(dev, steps):
     P = lgs.n_pixels(cams)
     out = {"workload": "indoor-2.8M-sh3-1332x876-training-step (fwd + L1 + bwd, graph, tight)",
            "steps_s": 1e3 / ms, "ms_per_step": ms, "mpix_s": P / 1e6 / (ms * 1e-3), "instances_K": int(st[2]),
-           "l1_loss": loss, "replays": n}
+           "l1_loss": loss, "replays": n, "tile": list(tune["tile"]), "warp_block": list(tune["block"]),
+           "persistent": tune["persistent"], "autotune": tune["timings"]}
     del r, g, graph
     torch.cuda.empty_cache()
     return out
 
 
-def run_scale(dev, steps):
+def run_scale(dev, steps, tile=(16, 16), block=None):
     """The scale scene: 30M SH3 Gaussians (256 clusters + background), 16 views
     of 1920x1080 in one batch (view groups of at most 2^16 tiles); forward with
     per-stage events, forward+backward
@@ -432,7 +436,7 @@ def run_scale(dev, steps):
     g = lgs.to_device(sc, dev)
     del sc
     n, V = g["means"].shape[0], len(cams)
-    r = batch.Renderer(g, cams, backward=True, tight=True)
+    r = batch.Renderer(g, cams, tile=tile, backward=True, tight=True, block=block)
     r.forward()
     pairs, cands = r.count_pairs()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -460,7 +464,8 @@ def run_scale(dev, steps):
     r.check()
     P = lgs.n_pixels(cams)
     pre_bytes = n * 236 + n * V * 69
-    out = {"workload": "scale-30M-sh3-16x1920x1080 (tight)", "frames_s": V / (ms_f * 1e-3),
+    out = {"workload": "scale-30M-sh3-16x1920x1080 (tight)", "tile": list(tile),
+           "warp_block": list(block) if block else None, "frames_s": V / (ms_f * 1e-3),
            "mpix_s": P / 1e6 / (ms_f * 1e-3), "ms_per_step": ms_f,
            "stage_ms": {"preprocess": float(sm[0]), "sort": float(sm[1]), "render": float(sm[2])},
            "fwd_bwd": {"frames_s": V / (ms_fb * 1e-3), "ms_per_step": ms_fb, "replays": nrep},
@@ -718,7 +723,7 @@ def run_ours(args, rank, world):
     if not args.no_batched:
         batched, n_batched = run_batched(dev, args.steps)
     indoor = None if args.no_indoor else run_indoor(dev, args.steps)
-    scale = None if args.no_scale else run_scale(dev, args.steps)
+    scale = None if args.no_scale else run_scale(dev, args.steps, tile, block)
     if rank != 0:
         return
     emission = "tight" if head.endswith("tight") else "rect"

@@ -109,13 +109,15 @@ struct __align__(16) BwdRed {
     uint32_t slot[RED_ROWS];   // batch index of the row's Gaussian
 };
 
+// The three 16-B records of a staged Gaussian sit at the same byte offset in
+// sV, sDE and sC; a warp's list holds that offset.
 template <int NW>
 struct BwdSmem {
     float4 sV[BWD_BATCH];        // (A, B, C, F), log2 domain
-    float2 sDE[BWD_BATCH];       // (D, E)
+    float4 sDE[BWD_BATCH];       // (D, E, -, -)
     float4 sC[BWD_BATCH];        // (r, g, b, list position + 1 as bits)
     uint8_t sM[BWD_BATCH];       // warp-block mask
-    uint8_t sL[NW][BWD_BATCH];   // per warp: batch indices of its set mask bits
+    uint16_t sL[NW][BWD_BATCH];  // per warp: byte offsets (16 x batch index) of its set mask bits
     uint32_t sId[BWD_BATCH];
     float sG[BWD_BATCH][9];      // per staged Gaussian: A, B, C, D, E, r, g, F, b gradients
     uint32_t sLast[NW];
@@ -267,7 +269,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
             S.sV[sl] = make_float4(-0.5f * LOG2E_B * co.x, -LOG2E_B * co.y, -0.5f * LOG2E_B * co.z,
                                    fmaf(Fn, LOG2E_B, __log2f(co.w)));
-            S.sDE[sl] = make_float2(Dn * LOG2E_B, En * LOG2E_B);
+            S.sDE[sl] = make_float4(Dn * LOG2E_B, En * LOG2E_B, 0.f, 0.f);
             S.sC[sl] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
             S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                            __fadd_rn(xy.y, xy.w), X0, Y0);
@@ -279,23 +281,23 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
         if (wlast > (uint32_t)begin) {
             // the warp's list of the batch (set mask bits up to its last
             // contributor), compacted in order and walked back to front
-            uint8_t* sLw = S.sL[warp];
+            uint16_t* sLw = S.sL[warp];
             int nl = 0;
             for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
                 const bool hit = jj < nb && ((S.sM[jj] >> warp) & 1u) && (uint32_t)(begin + jj) < wlast;
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-                if (hit) sLw[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
+                if (hit) sLw[nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(16 * jj);
                 nl += __popc(bal);
             }
             __syncwarp();
             int ns = 0;   // rows of the warp's buffer in use
 #pragma unroll 1
             for (int i = nl - 1; i >= 0; --i) {
-                const int g = sLw[i];
-                const float4 V = S.sV[g];
-                const float2 DE = S.sDE[g];
-                const float4 col = S.sC[g];
+                const int off = sLw[i];
+                const float4 V = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sV) + off);
+                const float4 DE = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sDE) + off);
+                const float4 col = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sC) + off);
                 const uint32_t pos = __float_as_uint(col.w);
                 const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
                              pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
@@ -343,7 +345,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                 const int cc = lane ^ (ns & 7);
                 R.R4[ns][cc] = make_float4(dp[0], dp[1], W0, W1);
                 R.R1[ns][cc] = W2;
-                if (lane == 0) R.slot[ns] = (uint32_t)g;
+                if (lane == 0) R.slot[ns] = (uint32_t)(off >> 4);
                 if (++ns == RED_ROWS) {
                     __syncwarp();
                     reduce_rows<TW, TH, WX, WY>(R, ns, S.sG, lane, warp);

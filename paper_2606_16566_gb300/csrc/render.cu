@@ -100,15 +100,23 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 }
 
 // ------------------------------------------------------------------ Local-GS
+// The three 16-B records of a staged Gaussian sit at the same byte offset in
+// sV, sDE and sC, so a warp's list holds that offset and the blend loop
+// addresses all three without index arithmetic.
 template <int NB>
 struct LocalSmem {
     float4 raw[2][3][NB];  // double-buffered cp.async landing zone: xy, conic, rgb records
     float4 sV[NB];         // (A, B, C, F), log2 domain
-    float2 sDE[NB];        // (D, E)
-    float4 sC[NB];         // (-r, -g, -b, clamp flag): colour negated, see the blend
+    float4 sDE[NB];        // (D, E, -, -)
+    float4 sC[NB];         // (-r, -g, -b, list position + 1 as bits): colour negated, see the blend
     uint8_t sM[NB];        // warp-block mask
-    uint8_t sL[8][NB];     // per warp: batch indices of its set mask bits, in order
+    uint16_t sL[8][NB];    // per warp: byte offsets (16 x batch index) of its set mask bits, in order
 };
+
+template <typename T>
+__device__ __forceinline__ const float4& at_offset(const T* base, int off) {
+    return *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + off);
+}
 
 // 16-byte asynchronous global -> shared copy (cp.async, cached in L2 only:
 // neighbouring tiles read the same Gaussians from L2) and its group fences.
@@ -232,11 +240,8 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
                 S.sV[sl] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
                                        fmaf(Fn, LOG2E, __log2f(co.w)));
-                S.sDE[sl] = make_float2(Dn * LOG2E, En * LOG2E);
-                // w: 1 when the 0.99 clamp can act (o > 0.9). With o <= 0.9,
-                // 2^pw stays below 0.91 even with the FP32 rounding of the
-                // hoisted exponent, so the clamp is the identity there
-                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, co.w > 0.9f ? 1.f : 0.f);
+                S.sDE[sl] = make_float4(Dn * LOG2E, En * LOG2E, 0.f, 0.f);
+                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, __uint_as_float(b0 + (uint32_t)sl + 1u));
                 S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                                __fadd_rn(xy.y, xy.w), X0, Y0);
             }
@@ -247,13 +252,13 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
         if (!warp_done) {
             // compact the warp's list: the batch indices whose mask bit for this
             // warp is set, in list order (one ballot per 32 candidates)
-            uint8_t* sL = S.sL[warp];
+            uint16_t* sL = S.sL[warp];
             int nl = 0;
             for (int c0 = 0; c0 < nb; c0 += 32) {
                 const int jj = c0 + lane;
                 const bool hit = jj < nb && ((S.sM[jj] >> warp) & 1u);
                 const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-                if (hit) sL[nl + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)jj;
+                if (hit) sL[nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(16 * jj);
                 nl += __popc(bal);
             }
             __syncwarp();
@@ -262,7 +267,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 const int iend = min(nl, i0 + 32);
 #pragma unroll 4
                 for (int i = i0; i < iend; ++i) {
-                    const int g = sL[i];
+                    const int off = sL[i];
                     if (VAR == VAR_LITERAL) {
                         if (__all_sync(0xffffffffu, lane_done())) { warp_done = true; break; }
                         if (COUNT) ++pairs;
@@ -270,21 +275,17 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                         if (__all_sync(0xffffffffu, lane_done())) break;
                         ++pairs;
                     }
-                    const float4 V = S.sV[g];
-                    const float2 DE = S.sDE[g];
-                    const float4 ncol = S.sC[g];
-                    const uint32_t idx = b0 + (uint32_t)g + 1u;
+                    const float4 V = at_offset(S.sV, off);
+                    const float4 DE = at_offset(S.sDE, off);
+                    const float4 ncol = at_offset(S.sC, off);
+                    const uint32_t idx = __float_as_uint(ncol.w);
                     const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
                                  pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
                     // -alpha = -min(0.99, 2^pw), negated so that the packed
                     // updates below need no separate negation
                     P nal;
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k) nal[k] = -ex2_approx(pw[k]);
-                    if (ncol.w != 0.f) {                     // warp-uniform
-#pragma unroll
-                        for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, nal[k]);
-                    }
+                    for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, -ex2_approx(pw[k]));
                     if (VAR == VAR_LITERAL) {
                         const P nw = pmul(nal, T);          // -w = -alpha T
                         C0 = pfma(bcast<PPL>(ncol.x), nw, C0);

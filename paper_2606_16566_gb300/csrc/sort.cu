@@ -814,11 +814,21 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(RsSrc<KT> src, const in
     if (first >= K) return;
     __syncwarp();
     const int64_t wfirst = first + warp * (RS_TILE / NW);
-#pragma unroll 4
-    for (int i = 0; i < RS_TILE / NW / 32; ++i) {
+    // all of the thread's keys first (independent loads in flight together),
+    // then the counting
+    uint32_t kk[RS_ITEMS];
+    uint32_t okm = 0;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
         const int64_t j = wfirst + i * 32 + lane;
-        uint32_t k = 0, v;
-        const bool ok = j < K && rs_load(src, j, k, v);
+        uint32_t v;
+        kk[i] = 0;
+        if (j < K && rs_load(RsSrc<KT>{src.k, nullptr, src.tiles, src.depth}, j, kk[i], v)) okm |= 1u << i;
+    }
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const uint32_t k = kk[i];
+        const bool ok = (okm >> i) & 1u;
         const uint32_t d = (k >> shift) & 0xffu;
         const uint32_t bal = __ballot_sync(0xffffffffu, ok);
         if (bal == 0u) continue;
@@ -905,12 +915,16 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint32_t d = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
+#ifdef LGS_RANK_MATCH
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+#else
         uint32_t peers = 0xffffffffu;
 #pragma unroll
         for (int b = 0; b < 9; ++b) {
             const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
+#endif
         const uint32_t b = d < 0x100u ? S.cnt[warp][d] : 0u;
         rk[i] = (uint16_t)(b + __popc(peers & lt));
         __syncwarp();
@@ -940,6 +954,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
         }
     }
     __syncthreads();
+#pragma unroll 4
     for (int j = t; j < (int)n_kept; j += RS_THREADS) {
         const uint32_t key = S.keys[j];
         const uint32_t d = (key >> shift) & 0xffu;
