@@ -141,7 +141,12 @@ typedef struct {
  * identical; only the speed differs. */
 #define LGS_FLAG_ONESWEEP 8
 
-/* Tile shape (tile_w x tile_h in {16x16, 8x32, 32x8}), render mode and flags.
+/* Tile shape, render mode and flags. Tiles of 256 pixels: 16x16, 8x32, 32x8.
+ * Larger tiles, 32x32, 16x32 and 32x16: sorted as one tile (fewer
+ * (Gaussian, tile) instances to duplicate and sort), rendered (and
+ * differentiated) by one CTA per 16x16 region, each walking the whole tile
+ * list with 8x8 warp blocks; LGS_MODE_LOCALGS only (the other modes return
+ * LGS_ERR_UNSUPPORTED for them).
  * batch = Gaussians the Local-GS render (LGS_MODE_LOCALGS) stages in shared
  * memory per round: 0 (= 256), 64, 128 or 256, else LGS_ERR_UNSUPPORTED; the
  * results do not depend on it. The other modes and the adjoint stage 256.
@@ -153,8 +158,9 @@ typedef struct {
  * with 16x2, 8x4 (2 x 4 blocks: the mask also culls by column half), 16x4 or
  * 8x8 blocks; 8x32 tiles with 8x4 or 8x8; 32x8 tiles with 32x1 or 8x8. Other
  * blocks, or a non-default block with LGS_MODE_PLAIN/LITERAL/GLOBAL, return
- * LGS_ERR_UNSUPPORTED. Outputs do not depend on the block layout (bit for bit);
- * only the work the mask saves does. Other entry points ignore the two fields. */
+ * LGS_ERR_UNSUPPORTED; the larger tiles take 8x8 blocks (0 x 0 or 8 x 8).
+ * Outputs do not depend on the block layout (bit for bit); only the work the
+ * mask saves does. Other entry points ignore the two fields. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t mode;

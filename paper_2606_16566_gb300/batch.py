@@ -29,7 +29,9 @@ import torch
 from . import _lib as L
 from . import lgs
 
-TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
+TILE_SHAPES = ((16, 16), (8, 32), (32, 8), (32, 32), (16, 32), (32, 16))
+# tiles of 256 pixels: the only ones of the plain and study kernels
+SMALL_TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
 
 
 MAX_GROUP_TILES = 1 << 16
@@ -268,6 +270,8 @@ def autotune(g, cams, mode="localgs", backward=False, shapes=TILE_SHAPES, persis
         torch.cuda.empty_cache()
 
     for tile in shapes:
+        if mode != "localgs" and tuple(tile) not in SMALL_TILE_SHAPES:
+            continue
         layouts = lgs.WARP_BLOCKS[tuple(tile)] if (blocks and mode == "localgs") else \
             lgs.WARP_BLOCKS[tuple(tile)][:1]
         for block in layouts:

@@ -197,17 +197,23 @@ __device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, float (*sG)
 // the CTA calls it with the same tile. Per lane, PPL pixels; their per-pixel
 // arithmetic runs packed two-wide when PPL = 2.
 template <int TW, int TH, int WX, int WY>
-__device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, uint32_t tile,
-                                         BwdSmem<Layout<TW, TH, WX, WY>::NW>& S) {
-    using Lay = Layout<TW, TH, WX, WY>;
+__device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, uint32_t work,
+                                         BwdSmem<TileLayout<TW, TH, WX, WY>::NW>& S) {
+    using Reg = Regions<TW, TH>;
+    constexpr int CW = Reg::CW, CH = Reg::CH;
+    using Lay = Layout<CW, CH, WX, WY>;
     constexpr int PPL = Lay::PPL, NT = Lay::NT, NW = Lay::NW;
     using P = Px<PPL>;
+    // work item = tile * (regions per tile) + region; the region (CW x CH
+    // pixels at X0, Y0) walks the whole list of its tile
+    const uint32_t tile = work / (uint32_t)Reg::N, reg = work % (uint32_t)Reg::N;
     const int view = view_of_tile(vs, tile);
     const ViewRec& c = vs.v[view];
     const uint32_t lt = tile - c.tile_off;
-    const int X0 = (int)(lt % (uint32_t)c.gx) * TW, Y0 = (int)(lt / (uint32_t)c.gx) * TH;
+    const int X0 = (int)(lt % (uint32_t)c.gx) * TW + (int)(reg % Reg::NX) * CW;
+    const int Y0 = (int)(lt / (uint32_t)c.gx) * TH + (int)(reg / Reg::NX) * CH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float Ox = (float)X0 + 0.5f * (TW - 1), Oy = (float)Y0 + 0.5f * (TH - 1);
+    const float Ox = (float)X0 + 0.5f * (CW - 1), Oy = (float)Y0 + 0.5f * (CH - 1);
     const int lx = (warp % Lay::NBX) * WX + lane % WX;
     uint2 r = p.ranges[tile];
     if (!LGS_CHECK(r.x <= r.y && (r.y == r.x || (int64_t)r.y <= p.status[LGS_ST_NUM_INSTANCES]), 21, p.status))
@@ -222,7 +228,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
     for (int k = 0; k < PPL; ++k) {
         const int ly = (warp / Lay::NBX) * WY + lane / WX + k * (WY / 2);
         const int px = X0 + lx, py = Y0 + ly;
-        const float xl = (float)lx - 0.5f * (TW - 1), yl = (float)ly - 0.5f * (TH - 1);
+        const float xl = (float)lx - 0.5f * (CW - 1), yl = (float)ly - 0.5f * (CH - 1);
         bx2[k] = xl * xl;
         bxy[k] = xl * yl;
         by2[k] = yl * yl;
@@ -271,7 +277,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                                    fmaf(Fn, LOG2E_B, __log2f(co.w)));
             S.sDE[sl] = make_float4(Dn * LOG2E_B, En * LOG2E_B, 0.f, 0.f);
             S.sC[sl] = make_float4(col.x, col.y, col.z, __uint_as_float(pos + 1u));
-            S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
+            S.sM[sl] = (uint8_t)block_mask<CW, CH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                            __fadd_rn(xy.y, xy.w), X0, Y0);
             S.sId[sl] = id;
 #pragma unroll
@@ -348,14 +354,14 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                 if (lane == 0) R.slot[ns] = (uint32_t)(off >> 4);
                 if (++ns == RED_ROWS) {
                     __syncwarp();
-                    reduce_rows<TW, TH, WX, WY>(R, ns, S.sG, lane, warp);
+                    reduce_rows<CW, CH, WX, WY>(R, ns, S.sG, lane, warp);
                     __syncwarp();
                     ns = 0;
                 }
             }
             if (ns > 0) {
                 __syncwarp();
-                reduce_rows<TW, TH, WX, WY>(R, ns, S.sG, lane, warp);
+                reduce_rows<CW, CH, WX, WY>(R, ns, S.sG, lane, warp);
                 __syncwarp();
             }
         }
@@ -391,30 +397,32 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
     }
 }
 
-// One CTA per tile (shared memory: the dynamic allocation of the launch).
+// One CTA per (tile, region) (shared memory: the dynamic allocation of the launch).
 template <int TW, int TH, int WX, int WY>
-__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_bwd_localgs(BwdParams p, Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_bwd_localgs(BwdParams p, Views vs) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
-    auto& S = *reinterpret_cast<BwdSmem<Layout<TW, TH, WX, WY>::NW>*>(bwd_smem);
+    auto& S = *reinterpret_cast<BwdSmem<TileLayout<TW, TH, WX, WY>::NW>*>(bwd_smem);
     bwd_tile<TW, TH, WX, WY>(p, vs, blockIdx.x, S);
 }
 
-// Persistent CTAs: each pulls the next tile index from the work-queue counter
-// LGS_ST_QUEUE_BWD (zeroed by the launcher) until all tiles are taken.
+// Persistent CTAs: each pulls the next (tile, region) work item from the
+// work-queue counter LGS_ST_QUEUE_BWD (zeroed by the launcher) until all are
+// taken.
 template <int TW, int TH, int WX, int WY>
-__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_bwd_localgs_persistent(BwdParams p,
-                                                                                         Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_bwd_localgs_persistent(BwdParams p,
+                                                                                             Views vs) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
-    auto& S = *reinterpret_cast<BwdSmem<Layout<TW, TH, WX, WY>::NW>*>(bwd_smem);
-    __shared__ uint32_t s_tile;
+    auto& S = *reinterpret_cast<BwdSmem<TileLayout<TW, TH, WX, WY>::NW>*>(bwd_smem);
+    __shared__ uint32_t s_work;
     unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE_BWD);
+    const uint32_t n_work = vs.n_tiles * (uint32_t)Regions<TW, TH>::N;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(q, 1ull);
+        if (threadIdx.x == 0) s_work = (uint32_t)atomicAdd(q, 1ull);
         __syncthreads();
-        const uint32_t tile = s_tile;
+        const uint32_t work = s_work;
         __syncthreads();
-        if (tile >= vs.n_tiles) break;
-        bwd_tile<TW, TH, WX, WY>(p, vs, tile, S);
+        if (work >= n_work) break;
+        bwd_tile<TW, TH, WX, WY>(p, vs, work, S);
         __syncthreads();
     }
 }
@@ -782,13 +790,14 @@ __global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) 
 
 template <int TW, int TH, int WX, int WY>
 lgs_status launch_bwd_layout(const BwdParams& bp, const Views& vs, bool persistent, cudaStream_t s) {
-    using Lay = Layout<TW, TH, WX, WY>;
+    using Lay = TileLayout<TW, TH, WX, WY>;
     const int smem = (int)sizeof(BwdSmem<Lay::NW>);
+    const uint32_t n_work = vs.n_tiles * (uint32_t)Regions<TW, TH>::N;
     if (!persistent) {
         auto k = render_bwd_localgs<TW, TH, WX, WY>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return LGS_ERR_CUDA;
-        k<<<vs.n_tiles, Lay::NT, smem, s>>>(bp, vs);
+        k<<<n_work, Lay::NT, smem, s>>>(bp, vs);
         return cuda_status(cudaGetLastError());
     }
     auto k = render_bwd_localgs_persistent<TW, TH, WX, WY>;
@@ -800,7 +809,7 @@ lgs_status launch_bwd_layout(const BwdParams& bp, const Views& vs, bool persiste
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Lay::NT, smem);
-    const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+    const unsigned g = (unsigned)min((int64_t)n_work, (int64_t)max(1, sms * max(per_sm, 1)));
     k<<<g, Lay::NT, smem, s>>>(bp, vs);
     return cuda_status(cudaGetLastError());
 }
@@ -808,6 +817,10 @@ lgs_status launch_bwd_layout(const BwdParams& bp, const Views& vs, bool persiste
 template <int TW, int TH>
 lgs_status launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, int wx, int wy, bool persistent,
                              cudaStream_t s) {
+    if constexpr (Regions<TW, TH>::SPLIT) {
+        // large tiles: Local-GS adjoint in 8x8 blocks only (checked on the host)
+        return launch_bwd_layout<TW, TH, 8, 8>(bp, vs, persistent, s);
+    } else {
     if (mode == LGS_MODE_PLAIN) {
         render_bwd_plain<TW, TH><<<vs.n_tiles, 256, 0, s>>>(bp, vs);
         return cuda_status(cudaGetLastError());
@@ -818,6 +831,7 @@ lgs_status launch_render_bwd(const BwdParams& bp, const Views& vs, int mode, int
         if (wx == 16 && wy == 4) return launch_bwd_layout<16, 16, 16, 4>(bp, vs, persistent, s);
     }
     return launch_bwd_layout<TW, TH, 8, 8>(bp, vs, persistent, s);
+    }
 }
 
 }  // namespace lgs
@@ -873,10 +887,16 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     if (persistent && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
     int wx = 0, wy = 0;
     if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
-    if (cfg->mode != LGS_MODE_LOCALGS && (wx != cfg->tile_w || wy != cfg->tile_h / 8)) return LGS_ERR_UNSUPPORTED;
-    if (cfg->tile_w == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, wx, wy, persistent, s);
-    else if (cfg->tile_w == 8) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);
-    else st = launch_render_bwd<32, 8>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    if (cfg->mode != LGS_MODE_LOCALGS &&
+        (split_tile(cfg->tile_w, cfg->tile_h) || wx != cfg->tile_w || wy != cfg->tile_h / 8))
+        return LGS_ERR_UNSUPPORTED;
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    if (tw == 16 && th == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else if (tw == 8 && th == 32) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else if (tw == 32 && th == 8) st = launch_render_bwd<32, 8>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else if (tw == 32 && th == 32) st = launch_render_bwd<32, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else if (tw == 16 && th == 32) st = launch_render_bwd<16, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);
+    else st = launch_render_bwd<32, 16>(bp, vs, cfg->mode, wx, wy, persistent, s);
     if (st != LGS_OK) return st;
     PreBwdParams pp;
     pp.means = g->means; pp.scales = g->scales; pp.quats = g->quats; pp.sh = g->sh; pp.n = g->n;

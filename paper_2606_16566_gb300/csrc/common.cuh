@@ -299,6 +299,21 @@ struct Layout {
     static_assert(32 % WX == 0 || WX == 32, "a warp row is whole lanes");
 };
 
+// CTA regions of a sort tile: a tile of 256 pixels is one region; the larger
+// tiles (32x32, 16x32, 32x16) are split into 16x16 regions, one CTA each, all
+// walking the tile's one list. Larger tiles mean fewer (Gaussian, tile)
+// instances to sort; the regions keep the warp blocks and the CTA size of the
+// 256-pixel tiles.
+template <int TW, int TH>
+struct Regions {
+    static constexpr bool SPLIT = TW * TH > 256;
+    static constexpr int CW = SPLIT ? 16 : TW, CH = SPLIT ? 16 : TH;
+    static constexpr int NX = TW / CW, NY = TH / CH, N = NX * NY;
+};
+
+template <int TW, int TH, int WX, int WY>
+using TileLayout = Layout<Regions<TW, TH>::CW, Regions<TW, TH>::CH, WX, WY>;
+
 // P pixels' worth of one float, with the packed FP32 operations on two.
 template <int P> struct Px;
 template <> struct Px<1> {

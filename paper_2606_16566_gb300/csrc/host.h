@@ -12,14 +12,25 @@ namespace lgs {
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline bool tile_shape_ok(int tw, int th) {
-    return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8);
+    return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8) ||
+           (tw == 32 && th == 32) || (tw == 16 && th == 32) || (tw == 32 && th == 16);
 }
+
+// Tiles of more than 256 pixels: sorted as one tile, rendered as 16x16 regions.
+inline bool split_tile(int tw, int th) { return tw * th > 256; }
 
 // The Local-GS render's warp block (see lgs_config): 0 x 0 selects the
 // paper's full-width strips; returns false for an unsupported block.
 inline bool warp_block(const lgs_config* cfg, int* wx, int* wy) {
     const int tw = cfg->tile_w, th = cfg->tile_h;
     int x = cfg->warp_w, y = cfg->warp_h;
+    if (split_tile(tw, th)) {
+        // the 16x16 regions of a large tile run in 8x8 blocks
+        if (!((x == 0 && y == 0) || (x == 8 && y == 8))) return false;
+        *wx = 8;
+        *wy = 8;
+        return true;
+    }
     if (x == 0 && y == 0) { x = tw; y = th / 8; }
     const bool ok = (x == tw && y == th / 8) || (x == 8 && y == 8) ||
                     (tw == 16 && th == 16 && ((x == 8 && y == 4) || (x == 16 && y == 4)));

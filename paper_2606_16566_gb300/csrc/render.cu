@@ -142,20 +142,26 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int VAR_CONTRACT = 0, VAR_LITERAL = 1, VAR_GLOBAL = 2;
 constexpr float INF_F = __builtin_huge_valf();
 
+// One CTA region of one tile: work item w = tile * (regions per tile) + region.
+// The region (CW x CH pixels at X0, Y0) walks the whole list of its tile.
 template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
-__device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t tile,
+__device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t work,
                                              LocalSmem<NB>& S) {
-    using Lay = Layout<TW, TH, WX, WY>;
+    using Reg = Regions<TW, TH>;
+    constexpr int CW = Reg::CW, CH = Reg::CH;
+    using Lay = Layout<CW, CH, WX, WY>;
     constexpr int PPL = Lay::PPL, NT = Lay::NT;
     static_assert(NB == 64 || NB == 128 || NB == 256, "staging batch of 64, 128 or 256 Gaussians");
     static_assert(NB % NT == 0 || NT % NB == 0, "whole staging slots per thread");
     using P = Px<PPL>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+    const uint32_t tile = work / (uint32_t)Reg::N, reg = work % (uint32_t)Reg::N;
     const int view = view_of_tile(vs, tile);
     const ViewRec& cam = vs.v[view];
     const uint32_t lt = tile - cam.tile_off;
-    const int X0 = (int)(lt % (uint32_t)cam.gx) * TW, Y0 = (int)(lt / (uint32_t)cam.gx) * TH;
+    const int X0 = (int)(lt % (uint32_t)cam.gx) * TW + (int)(reg % Reg::NX) * CW;
+    const int Y0 = (int)(lt / (uint32_t)cam.gx) * TH + (int)(reg / Reg::NX) * CH;
     uint2 rg = p.ranges[tile];
     uint32_t start = rg.x, count = rg.y - rg.x;
     // the tile's list must lie inside the sorted instances (checked build; it
@@ -165,8 +171,8 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
         count = 0;
 
     constexpr bool global_frame = VAR == VAR_GLOBAL;
-    const float Ox = global_frame ? 0.f : (float)X0 + 0.5f * (TW - 1);
-    const float Oy = global_frame ? 0.f : (float)Y0 + 0.5f * (TH - 1);
+    const float Ox = global_frame ? 0.f : (float)X0 + 0.5f * (CW - 1);
+    const float Oy = global_frame ? 0.f : (float)Y0 + 0.5f * (CH - 1);
     // the lane's pixels: tile-local (lx, ly[k]); basis B = [x'^2, x'y', y'^2, x', y', 1]
     const int lx = (warp % Lay::NBX) * WX + lane % WX;
     int ly[PPL];
@@ -177,8 +183,8 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
     for (int k = 0; k < PPL; ++k) {
         ly[k] = (warp / Lay::NBX) * WY + lane / WX + k * (WY / 2);
         inside[k] = X0 + lx < cam.W && Y0 + ly[k] < cam.H;
-        const float xl = global_frame ? (float)(X0 + lx) : (float)lx - 0.5f * (TW - 1);
-        const float yl = global_frame ? (float)(Y0 + ly[k]) : (float)ly[k] - 0.5f * (TH - 1);
+        const float xl = global_frame ? (float)(X0 + lx) : (float)lx - 0.5f * (CW - 1);
+        const float yl = global_frame ? (float)(Y0 + ly[k]) : (float)ly[k] - 0.5f * (CH - 1);
         bx2[k] = xl * xl;
         bxy[k] = xl * yl;
         by2[k] = yl * yl;
@@ -242,7 +248,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                                        fmaf(Fn, LOG2E, __log2f(co.w)));
                 S.sDE[sl] = make_float4(Dn * LOG2E, En * LOG2E, 0.f, 0.f);
                 S.sC[sl] = make_float4(-col.x, -col.y, -col.z, __uint_as_float(b0 + (uint32_t)sl + 1u));
-                S.sM[sl] = (uint8_t)block_mask<TW, TH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
+                S.sM[sl] = (uint8_t)block_mask<CW, CH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                                __fadd_rn(xy.y, xy.w), X0, Y0);
             }
         }
@@ -340,29 +346,31 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                   (unsigned long long)cands);
 }
 
-// One CTA per tile.
+// One CTA per (tile, region).
 template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
-__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_localgs(RenderParams p, Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_localgs(RenderParams p, Views vs) {
     __shared__ LocalSmem<NB> S;
     localgs_tile<TW, TH, WX, WY, COUNT, VAR, NB>(p, vs, blockIdx.x, S);
 }
 
-// Persistent CTAs: each pulls the next tile index from a work-queue counter
-// (status word LGS_ST_QUEUE, zeroed by the launcher) until all tiles are taken,
-// so uneven tile lists and uneven view sizes balance across the SMs.
+// Persistent CTAs: each pulls the next (tile, region) work item from a
+// work-queue counter (status word LGS_ST_QUEUE, zeroed by the launcher) until
+// all are taken, so uneven tile lists and uneven view sizes balance across
+// the SMs.
 template <int TW, int TH, int WX, int WY, bool COUNT, int NB>
-__global__ void __launch_bounds__(Layout<TW, TH, WX, WY>::NT) render_localgs_persistent(RenderParams p,
-                                                                                     Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_localgs_persistent(RenderParams p,
+                                                                                         Views vs) {
     __shared__ LocalSmem<NB> S;
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_work;
     unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE);
+    const uint32_t n_work = vs.n_tiles * (uint32_t)Regions<TW, TH>::N;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(q, 1ull);
+        if (threadIdx.x == 0) s_work = (uint32_t)atomicAdd(q, 1ull);
         __syncthreads();
-        const uint32_t tile = s_tile;
+        const uint32_t work = s_work;
         __syncthreads();
-        if (tile >= vs.n_tiles) break;
-        localgs_tile<TW, TH, WX, WY, COUNT, VAR_CONTRACT, NB>(p, vs, tile, S);
+        if (work >= n_work) break;
+        localgs_tile<TW, TH, WX, WY, COUNT, VAR_CONTRACT, NB>(p, vs, work, S);
         __syncthreads();
     }
 }
@@ -424,8 +432,9 @@ __global__ void __launch_bounds__(256) render_plain(RenderParams p, Views vs) {
 template <int TW, int TH, int WX, int WY, int NB>
 lgs_status launch_contract(const RenderParams& p, const Views& vs, bool count, bool persistent,
                            cudaStream_t s) {
-    constexpr int NT = Layout<TW, TH, WX, WY>::NT;
-    const dim3 grid(vs.n_tiles), block(NT);
+    constexpr int NT = TileLayout<TW, TH, WX, WY>::NT;
+    const uint32_t n_work = vs.n_tiles * (uint32_t)Regions<TW, TH>::N;
+    const dim3 grid(n_work), block(NT);
     if (!persistent) {
         if (count) render_localgs<TW, TH, WX, WY, true, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
         else       render_localgs<TW, TH, WX, WY, false, VAR_CONTRACT, NB><<<grid, block, 0, s>>>(p, vs);
@@ -438,12 +447,12 @@ lgs_status launch_contract(const RenderParams& p, const Views& vs, bool count, b
     if (count) {
         auto k = render_localgs_persistent<TW, TH, WX, WY, true, NB>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, 0);
-        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+        const unsigned g = (unsigned)min((int64_t)n_work, (int64_t)max(1, sms * max(per_sm, 1)));
         k<<<g, block, 0, s>>>(p, vs);
     } else {
         auto k = render_localgs_persistent<TW, TH, WX, WY, false, NB>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, 0);
-        const unsigned g = (unsigned)min((int64_t)vs.n_tiles, (int64_t)max(1, sms * max(per_sm, 1)));
+        const unsigned g = (unsigned)min((int64_t)n_work, (int64_t)max(1, sms * max(per_sm, 1)));
         k<<<g, block, 0, s>>>(p, vs);
     }
     return cuda_status(cudaGetLastError());
@@ -470,6 +479,10 @@ lgs_status launch_variant(const RenderParams& p, const Views& vs, bool count, cu
 template <int TW, int TH>
 lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, int batch, int wx, int wy,
                          bool count, bool persistent, cudaStream_t s) {
+    if constexpr (Regions<TW, TH>::SPLIT) {
+        // large tiles: Local-GS contract in 8x8 blocks only (checked on the host)
+        return launch_layout<TW, TH, 8, 8>(p, vs, batch, count, persistent, s);
+    } else {
     if (mode == LGS_MODE_PLAIN) {
         const dim3 grid(vs.n_tiles), block(256);
         if (count) render_plain<TW, TH, true><<<grid, block, 0, s>>>(p, vs);
@@ -484,6 +497,7 @@ lgs_status launch_render(const RenderParams& p, const Views& vs, int mode, int b
         if (wx == 16 && wy == 4) return launch_layout<16, 16, 16, 4>(p, vs, batch, count, persistent, s);
     }
     return launch_layout<TW, TH, 8, 8>(p, vs, batch, count, persistent, s);
+    }
 }
 
 }  // namespace lgs
@@ -520,9 +534,15 @@ extern "C" lgs_status lgs_render_fwd(const lgs_pre_out* pre, const uint32_t* val
     const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
     int wx = 0, wy = 0;
     if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
-    if (cfg->mode != LGS_MODE_LOCALGS && (wx != cfg->tile_w || wy != cfg->tile_h / 8)) return LGS_ERR_UNSUPPORTED;
+    if (cfg->mode != LGS_MODE_LOCALGS &&
+        (split_tile(cfg->tile_w, cfg->tile_h) || wx != cfg->tile_w || wy != cfg->tile_h / 8))
+        return LGS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cfg->tile_w == 16) return launch_render<16, 16>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
-    if (cfg->tile_w == 8) return launch_render<8, 32>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
-    return launch_render<32, 8>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    if (tw == 16 && th == 16) return launch_render<16, 16>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    if (tw == 8 && th == 32) return launch_render<8, 32>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    if (tw == 32 && th == 8) return launch_render<32, 8>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    if (tw == 32 && th == 32) return launch_render<32, 32>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    if (tw == 16 && th == 32) return launch_render<16, 32>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
+    return launch_render<32, 16>(p, vs, cfg->mode, batch, wx, wy, count, persistent, s);
 }

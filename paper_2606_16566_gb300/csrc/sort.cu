@@ -1189,15 +1189,17 @@ static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
     KT *ka = reinterpret_cast<KT*>(ws->ak), *kb = reinterpret_cast<KT*>(ws->bk);
     uint32_t *va = (passes & 1) ? ws->bv : a.vals, *vb = (passes & 1) ? a.vals : ws->bv;
     if (a.tight) {
-        if (vs->tile_w == 16)
-            emit_pairs_tight<16, 16, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
-                                                            m, a.n, a.d_status, capacity, *vs, ka, va);
-        else if (vs->tile_w == 8)
-            emit_pairs_tight<8, 32, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
-                                                           m, a.n, a.d_status, capacity, *vs, ka, va);
-        else
-            emit_pairs_tight<32, 8, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec,
-                                                           m, a.n, a.d_status, capacity, *vs, ka, va);
+#define LGS_EMIT_TIGHT(TW_, TH_)                                                                          \
+    emit_pairs_tight<TW_, TH_, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec, m, a.n, \
+                                                      a.d_status, capacity, *vs, ka, va)
+        const int tw = vs->tile_w, th = vs->tile_h;
+        if (tw == 16 && th == 16) LGS_EMIT_TIGHT(16, 16);
+        else if (tw == 8 && th == 32) LGS_EMIT_TIGHT(8, 32);
+        else if (tw == 32 && th == 8) LGS_EMIT_TIGHT(32, 8);
+        else if (tw == 32 && th == 32) LGS_EMIT_TIGHT(32, 32);
+        else if (tw == 16 && th == 32) LGS_EMIT_TIGHT(16, 32);
+        else LGS_EMIT_TIGHT(32, 16);
+#undef LGS_EMIT_TIGHT
     } else {
         emit_pairs<KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, a.pre->rect, m, a.n, a.d_status,
                                           capacity, *vs, ka, va);
@@ -1272,17 +1274,18 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     const float4* pco = reinterpret_cast<const float4*>(pre->conic);
     const uint4* pem = reinterpret_cast<const uint4*>(pre->emit);
     const unsigned eg = (unsigned)ceil_div(m, 256);
-    if (!tight)
-        gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
-    else if (vs->tile_w == 16)
-        count_tight<16, 16><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
-                                               ws->tiles_s, ws->erec);
-    else if (vs->tile_w == 8)
-        count_tight<8, 32><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
-                                              ws->tiles_s, ws->erec);
-    else
-        count_tight<32, 8><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs,
-                                              ws->tiles_s, ws->erec);
+#define LGS_COUNT_TIGHT(TW_, TH_)                                                                       \
+    count_tight<TW_, TH_><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs, ws->tiles_s, \
+                                             ws->erec)
+    const int tw = vs->tile_w, th = vs->tile_h;
+    if (!tight) gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
+    else if (tw == 16 && th == 16) LGS_COUNT_TIGHT(16, 16);
+    else if (tw == 8 && th == 32) LGS_COUNT_TIGHT(8, 32);
+    else if (tw == 32 && th == 8) LGS_COUNT_TIGHT(32, 8);
+    else if (tw == 32 && th == 32) LGS_COUNT_TIGHT(32, 32);
+    else if (tw == 16 && th == 32) LGS_COUNT_TIGHT(16, 32);
+    else LGS_COUNT_TIGHT(32, 16);
+#undef LGS_COUNT_TIGHT
     const int64_t nscan = ceil_div(m, SCAN_TILE);
     scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);

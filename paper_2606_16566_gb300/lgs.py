@@ -15,7 +15,7 @@ import torch
 
 from . import _lib as L
 
-_TILES = {(16, 16), (8, 32), (32, 8)}
+_TILES = {(16, 16), (8, 32), (32, 8), (32, 32), (16, 32), (32, 16)}
 
 
 def _ptr(t):
@@ -27,9 +27,11 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-# warp blocks of the Local-GS render per tile shape (the first is the paper's layout)
+# warp blocks of the Local-GS render per tile shape (the first is the default:
+# the paper's layout for 256-pixel tiles; larger tiles are rendered as 16x16
+# regions of 8x8 blocks)
 WARP_BLOCKS = {(16, 16): ((16, 2), (8, 4), (16, 4), (8, 8)), (8, 32): ((8, 4), (8, 8)),
-               (32, 8): ((32, 1), (8, 8))}
+               (32, 8): ((32, 1), (8, 8)), (32, 32): ((8, 8),), (16, 32): ((8, 8),), (32, 16): ((8, 8),)}
 
 
 def config(tile=(16, 16), mode="localgs", flags=0, batch=0, block=None) -> L.lgs_config:

@@ -173,3 +173,80 @@ def test_block_layout_persistent_graph_adjoint(tile, block):
     for k in ("means", "scales", "quats", "opacities", "sh"):
         d = (rs[0].grads[k] - rs[1].grads[k]).norm() / rs[0].grads[k].norm().clamp_min(1e-30)
         assert d.item() <= 1e-4, k
+
+
+BIG = [(32, 32), (16, 32), (32, 16)]
+
+
+@pytest.mark.parametrize("tight", [False, True])
+@pytest.mark.parametrize("tile", BIG)
+def test_large_tiles_match_oracle(tile, tight):
+    """Tiles of more than 256 pixels (sorted as one tile, rendered by one CTA
+    per 16x16 region in 8x8 blocks) against the oracle on the same tiles:
+    lists, contributor counts and images at the parity bar, ragged sizes,
+    several views in one batch."""
+    sc, cams = scenes.random_small(5000, seed=311, width=203, height=151, log_scale_mean=-2.8)
+    cams = cams + [scenes.look_at((1.0, 2.0, -4.0), (0, 0, 0), 97, 61, 60.0)]
+    g = lgs.to_device(sc)
+    res = lgs.render(g, cams, tile=tile, flags=L.FLAG_TIGHT if tight else 0)
+    for v in range(len(cams)):
+        view = to_numpy_view(res, v, cams, 5000, tile)
+        rep, _ = full_view_parity(sc, cams[v], view, tile, tight=tight)
+        print(tile, tight, v, rep)
+        assert not rep["unexplained_tiles"], rep["unexplained_tiles"][:10]
+        assert rep["n_contrib_mismatch"] == 0, rep
+        assert_image_parity(rep, f"tile {tile} view {v}")
+
+
+@pytest.mark.parametrize("tile", BIG)
+def test_large_tiles_pair_count_and_persistent(tile):
+    sc, cams = scenes.random_small(3000, seed=31, width=200, height=160)
+    g = lgs.to_device(sc)
+    ref = _frame(g, cams, tile, L.FLAG_COUNT)
+    st = ref[3]
+    o = oracle.render(sc, cams[0], tile[0], tile[1])
+    want = oracle.localgs_pairs(o, cams[0], tile[0], tile[1], block=(8, 8))
+    print(tile, int(st[L.ST_PAIRS]), want)
+    assert want <= st[L.ST_PAIRS] <= 1.02 * want
+    got = _frame(g, cams, tile, L.FLAG_PERSISTENT)
+    for a, b in zip(ref[:3], got[:3]):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("tile", BIG)
+def test_large_tiles_adjoint_matches_oracle(tile):
+    sc, cams = scenes.random_small(700, seed=74, width=93, height=71, sh_degree=3, log_scale_mean=-2.6)
+    cam = dict(cams[0])
+    cam["bg"] = np.array([0.3, 0.1, 0.6], np.float32)
+    rng = np.random.default_rng(7)
+    H, W = cam["height"], cam["width"]
+    g_rgb = rng.standard_normal((3, H, W)).astype(np.float32)
+    g_T = rng.standard_normal((H, W)).astype(np.float32)
+    g = lgs.to_device(sc)
+    cfg = lgs.config(tile)
+    st = lgs.new_status()
+    pre = lgs.preprocess(g, [cam], cfg, status=st)
+    _, vals, ranges = lgs.sort(pre, 700, [cam], cfg, 1 << 18, status=st)
+    rgb, T, nc = lgs.render_fwd(pre, vals, ranges, [cam], cfg, status=st)
+    gr = lgs.render_bwd(g, [cam], cfg, pre, vals, ranges, T, nc, torch.from_numpy(g_rgb).cuda().reshape(-1),
+                        torch.from_numpy(g_T).cuda().reshape(-1), status=st)
+    torch.cuda.synchronize()
+    assert lgs.read_status(st)[L.ST_CODE] == 0
+    ref = oracle.backward(sc, cam, g_rgb, g_T, tile[0], tile[1])
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        r = _rel(gr[k].cpu().numpy(), ref[k])
+        print(tile, k, r)
+        assert r <= 1e-3, (k, r)
+
+
+def test_large_tiles_reject_other_modes():
+    sc, cams = scenes.random_small(200, seed=9)
+    g = lgs.to_device(sc)
+    res = lgs.render(g, cams, tile=(32, 32))
+    for mode in ("plain", "literal", "global"):
+        with pytest.raises(L.LgsError) as e:
+            lgs.render_fwd(res["pre"], res["vals"], res["ranges"], cams, lgs.config((32, 32), mode))
+        assert e.value.code == L.LGS_ERR_UNSUPPORTED
+    with pytest.raises(L.LgsError) as e:
+        lgs.render_fwd(res["pre"], res["vals"], res["ranges"], cams, lgs.config((32, 32), block=(8, 4)))
+    assert e.value.code == L.LGS_ERR_UNSUPPORTED
