@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--block", default="paper",
                    help="warp block WxH of the Local-GS render with a fixed --tile (paper = full-width strips)")
     p.add_argument("--no-tiny", action="store_true", help="skip the 10k-Gaussian 256x256 configuration")
+    p.add_argument("--batch", type=int, default=0, help="with --profile: staging batch of the Local-GS render")
     p.add_argument("--sort", default="rts", choices=["rts", "onesweep"],
                    help="with --profile: radix passes as reduce-then-scan kernels or onesweep kernels")
     return p.parse_args()
@@ -522,7 +523,7 @@ def run_ours(args, rank, world):
         g = lgs.to_device(scene, dev)
         del scene
         r = batch.Renderer(g, cams, tile=tile, mode=args.mode, backward=args.backward, tight=args.tight,
-                           block=block)
+                           block=block, batch=args.batch)
         if args.backward:
             r.d_rgb.fill_(1.0 / r.d_rgb.numel())
         for _ in range(args.warmup + args.steps):
@@ -540,7 +541,7 @@ def run_ours(args, rank, world):
         pipe = Pipeline(g, cams, tile, int(probe["K"] * 1.05) + 1024)
         del probe
         flags = (L.FLAG_TIGHT if args.tight else 0) | (L.FLAG_ONESWEEP if args.sort == "onesweep" else 0)
-        cfg = lgs.config(tile, args.mode, flags, 0, block)
+        cfg = lgs.config(tile, args.mode, flags, args.batch, block)
         if args.backward:
             pipe.setup_backward()
         for _ in range(args.warmup + args.steps):

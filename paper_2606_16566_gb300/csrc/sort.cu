@@ -915,16 +915,12 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; ++i) {
         const uint32_t d = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
-#ifdef LGS_RANK_MATCH
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-#else
         uint32_t peers = 0xffffffffu;
 #pragma unroll
         for (int b = 0; b < 9; ++b) {
             const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
-#endif
         const uint32_t b = d < 0x100u ? S.cnt[warp][d] : 0u;
         rk[i] = (uint16_t)(b + __popc(peers & lt));
         __syncwarp();
