@@ -36,7 +36,10 @@
 
 namespace lgs {
 
-constexpr int BWD_BATCH = 256;
+#ifndef LGS_BWD_BATCH
+#define LGS_BWD_BATCH 256
+#endif
+constexpr int BWD_BATCH = LGS_BWD_BATCH;
 constexpr float LOG2E_B = 1.4426950408889634f;
 constexpr float LOG2_ALPHA_MIN_B = -7.9943534368588580f;
 
@@ -96,10 +99,11 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 // Per-warp buffer of the deferred reduction: up to RED_ROWS rows, one per
-// Gaussian of the warp's list. Row r holds, per lane, (dp of its first pixel,
-// dp of its second pixel (0 with one pixel per lane), W_r, W_g) in R4 and W_b
-// in R1, where dp = dL/dalpha alpha of a pixel and W_c = sum over the lane's
-// pixels of w g_c (w = alpha T, g = dL/drgb). Lane c of row r is stored at
+// Gaussian of the warp's list. Row r holds, per lane, (-dp of its first pixel,
+// -dp of its second pixel (0 with one pixel per lane), -W_r, -W_g) in R4 and
+// -W_b in R1, where dp = dL/dalpha alpha of a pixel and W_c = sum over the
+// lane's pixels of w g_c (w = alpha T, g = dL/drgb); the walk produces them
+// negated, and the reduction negates its sums back. Lane c of row r is stored at
 // column c ^ (r & 7), so that the row writes of the walk (one row, 32 lanes)
 // and the reads of the reduction (8 rows, 8 lanes each) hit distinct banks.
 constexpr int RED_ROWS = 8;
@@ -187,9 +191,10 @@ __device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, float (*sG)
         v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
     }
     if (q == 0 && e < ns) {
+        // the buffer holds -dp and -w g: the sums are negated back here
         float* dst = sG[R.slot[e]];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) atomicAdd(dst + k, v[k]);
+        for (int k = 0; k < 9; ++k) atomicAdd(dst + k, -v[k]);
     }
 }
 
@@ -219,7 +224,9 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
     if (!LGS_CHECK(r.x <= r.y && (r.y == r.x || (int64_t)r.y <= p.status[LGS_ST_NUM_INSTANCES]), 21, p.status))
         r.y = r.x;
 
-    P bx2, bxy, by2, bxl, byl, T, g0, g1, g2, tail, Ag;
+    // carried negated (-<A, g>, -tail) so that the packed updates below need
+    // no separate negations
+    P bx2, bxy, by2, bxl, byl, T, g0, g1, g2, ntail, nAg;
     uint32_t last[PPL];
     uint32_t mylast = 0;
     const int64_t plane = (int64_t)c.W * c.H;
@@ -235,7 +242,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
         bxl[k] = xl;
         byl[k] = yl;
         T[k] = 1.f;
-        g0[k] = g1[k] = g2[k] = tail[k] = Ag[k] = 0.f;
+        g0[k] = g1[k] = g2[k] = ntail[k] = nAg[k] = 0.f;
         last[k] = 0;
         if (px < c.W && py < c.H) {
             const int64_t pix = (int64_t)py * c.W + px;
@@ -245,7 +252,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             T[k] = p.final_T[c.pix_off + pix];
             last[k] = p.n_contrib[c.pix_off + pix];
             const float gT = p.dL_dT ? p.dL_dT[c.pix_off + pix] : 0.f;
-            tail[k] = T[k] * (c.bg[0] * g0[k] + c.bg[1] * g1[k] + c.bg[2] * g2[k] + gT);
+            ntail[k] = -(T[k] * (c.bg[0] * g0[k] + c.bg[1] * g1[k] + c.bg[2] * g2[k] + gT));
         }
         mylast = max(mylast, last[k]);
     }
@@ -316,32 +323,32 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;   // nothing to reduce
                 // branch-free: pixels that do not contribute get alpha 0, which
-                // leaves T and the colour behind exactly as they were
-                P e2, al, inv, ac;
+                // leaves T and the colour behind exactly as they were. Carried
+                // negated: nal = -alpha, nac = -alpha of a contributing pixel
+                P e2, nal, inv, nac;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     e2[k] = ex2_approx_b(pw[k]);
-                    al[k] = fminf(0.99f, e2[k]);
-                    inv[k] = __fdividef(1.f, 1.f - al[k]);   // 1 - alpha >= 0.01
-                    ac[k] = contrib[k] ? al[k] : 0.f;
+                    nal[k] = fmaxf(-0.99f, -e2[k]);
+                    inv[k] = __fdividef(1.f, 1.f + nal[k]);  // 1 - alpha >= 0.01
+                    nac[k] = contrib[k] ? nal[k] : 0.f;
                 }
                 const P Tk = pmul(T, inv);
-                const P w = pmul(ac, Tk);
-                // <rgb_k - A_k, g>, and A <- alpha rgb + (1 - alpha) A carried as <A, g>
-                const P cg = padd(pfma(bcast<PPL>(col.z), g2, pfma(bcast<PPL>(col.y), g1,
-                                                                   pmul(bcast<PPL>(col.x), g0))),
-                                  pneg(Ag));
-                const P dal = pfma(Tk, cg, pneg(pmul(tail, inv)));
-                Ag = pfma(ac, cg, Ag);
-                const P dal_al = pmul(dal, al);
-                float dp[2] = {0.f, 0.f};
+                const P nw = pmul(nac, Tk);                  // -w = -alpha T
+                // <rgb_k - A_k, g>, and A <- alpha rgb + (1 - alpha) A carried as -<A, g>
+                const P cg = pfma(bcast<PPL>(col.z), g2, pfma(bcast<PPL>(col.y), g1,
+                                                               pfma(bcast<PPL>(col.x), g0, nAg)));
+                const P dal = pfma(ntail, inv, pmul(Tk, cg));  // dL/dalpha
+                nAg = pfma(nac, cg, nAg);
+                const P ndal = pmul(dal, nal);               // -dL/dalpha alpha
+                float ndp[2] = {0.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     T[k] = contrib[k] ? Tk[k] : T[k];
-                    dp[k] = (contrib[k] && !(e2[k] > 0.99f)) ? dal_al[k] : 0.f;
+                    ndp[k] = (contrib[k] && !(e2[k] > 0.99f)) ? ndal[k] : 0.f;
                 }
-                // the lane's colour sums over its pixels
-                const P wg0 = pmul(w, g0), wg1 = pmul(w, g1), wg2 = pmul(w, g2);
+                // the lane's colour sums over its pixels (negated, like dp)
+                const P wg0 = pmul(nw, g0), wg1 = pmul(nw, g1), wg2 = pmul(nw, g2);
                 float W0 = wg0[0], W1 = wg1[0], W2 = wg2[0];
                 if (PPL == 2) {
                     W0 += wg0[PPL - 1];
@@ -349,7 +356,7 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                     W2 += wg2[PPL - 1];
                 }
                 const int cc = lane ^ (ns & 7);
-                R.R4[ns][cc] = make_float4(dp[0], dp[1], W0, W1);
+                R.R4[ns][cc] = make_float4(ndp[0], ndp[1], W0, W1);
                 R.R1[ns][cc] = W2;
                 if (lane == 0) R.slot[ns] = (uint32_t)(off >> 4);
                 if (++ns == RED_ROWS) {
@@ -398,8 +405,15 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
 }
 
 // One CTA per (tile, region) (shared memory: the dynamic allocation of the launch).
+// Five CTAs per SM: the register bound this sets (at most 102 per thread for
+// 128-thread CTAs) measured faster than the unbounded allocation (112, four
+// CTAs) and than six or eight CTAs with 128-Gaussian batches.
+#ifndef LGS_BWD_MIN_BLOCKS
+#define LGS_BWD_MIN_BLOCKS 5
+#endif
 template <int TW, int TH, int WX, int WY>
-__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_bwd_localgs(BwdParams p, Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT, LGS_BWD_MIN_BLOCKS) render_bwd_localgs(BwdParams p,
+                                                                                                     Views vs) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     auto& S = *reinterpret_cast<BwdSmem<TileLayout<TW, TH, WX, WY>::NW>*>(bwd_smem);
     bwd_tile<TW, TH, WX, WY>(p, vs, blockIdx.x, S);
@@ -409,8 +423,8 @@ __global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_bwd_loc
 // work-queue counter LGS_ST_QUEUE_BWD (zeroed by the launcher) until all are
 // taken.
 template <int TW, int TH, int WX, int WY>
-__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_bwd_localgs_persistent(BwdParams p,
-                                                                                             Views vs) {
+__global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT, LGS_BWD_MIN_BLOCKS)
+    render_bwd_localgs_persistent(BwdParams p, Views vs) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     auto& S = *reinterpret_cast<BwdSmem<TileLayout<TW, TH, WX, WY>::NW>*>(bwd_smem);
     __shared__ uint32_t s_work;

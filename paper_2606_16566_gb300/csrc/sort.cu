@@ -90,8 +90,10 @@ __device__ __forceinline__ int64_t sort_count(const int64_t* status, int64_t cap
 }
 
 // ------------------------------------------------------------------ scan of tiles
-__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce(const uint32_t* tiles, int64_t m,
+// Entries at or past the device count *mv (the visible entries) count as 0.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce(const uint32_t* tiles, int64_t m, const int64_t* mv,
                                                             uint64_t* block_sums) {
+    m = pass_count(mv, m);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     uint64_t s = 0;
 #pragma unroll
@@ -133,10 +135,11 @@ __global__ void __launch_bounds__(1024) scan_block_sums(uint64_t* block_sums, in
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* tiles, int64_t m,
+__global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* tiles, int64_t m, const int64_t* mv,
                                                                const uint64_t* block_sums,
                                                                uint32_t* offsets) {
     __shared__ uint32_t ws[32];
+    m = pass_count(mv, m);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     // blocked arrangement: thread t owns items [t*ITEMS, (t+1)*ITEMS) of the block
     uint32_t v[SCAN_ITEMS];
@@ -350,6 +353,39 @@ __device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t e) {
     return lo;
 }
 
+// Tight instance count of the entries the 32 lanes of a warp hold (lane
+// state L; a lane without an entry has L.wd = 0), returned to each lane. The
+// entries expand into column items that the lanes take 32 at a time (owner
+// found by a binary search over the inclusive column counts), so wide and
+// narrow Gaussians share the work evenly; cnt = the warp's 32 shared counters.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_tight_count(const TightLane& L, uint32_t* cnt) {
+    const int lane = threadIdx.x & 31;
+    cnt[lane] = 0u;
+    __syncwarp();
+    const uint32_t iw = warp_inclusive_sum(L.wd);
+    const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
+    const uint32_t ew = iw - L.wd;
+    for (uint32_t e0 = 0; e0 < items; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const int own = owner_lane(iw, e);
+        const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
+        const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
+        const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
+        const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
+        const TightBox ot = tight_box_of(L.tb, own);
+        if (e < items) {
+            int rlo, rhi;
+            const int k = tight_tile_rows(ot, (int)(ox0 + col) * TW, TW, TH, oy0, oy1, &rlo, &rhi);
+            if (k) atomicAdd(&cnt[own], (uint32_t)k);
+        }
+    }
+    __syncwarp();
+    const uint32_t r = cnt[lane];
+    __syncwarp();
+    return r;
+}
+
 // Tight instance count of every entry in depth order: tiles_sorted[j] =
 // instances that emission will write for entry order[j] (0 past the visible
 // entries).
@@ -363,8 +399,6 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
     if (wbase >= m) return;
-    const int lane = threadIdx.x & 31;
-    const int wofs = threadIdx.x & ~31;
     const bool valid = idx < m;
     const bool visible = idx < pass_count(mv, m);
     const uint32_t ent = visible ? order[idx] : 0u;
@@ -385,27 +419,8 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
     } else {
         L = tight_lane_load(ent, visible, rect, xy, conic, vs, n, rec, idx);
     }
-    cnt[threadIdx.x] = 0u;
-    __syncwarp();
-    const uint32_t iw = warp_inclusive_sum(L.wd);
-    const uint32_t items = __shfl_sync(0xffffffffu, iw, 31);
-    const uint32_t ew = iw - L.wd;
-    for (uint32_t e0 = 0; e0 < items; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        const int own = owner_lane(iw, e);
-        const uint32_t col = e - __shfl_sync(0xffffffffu, ew, own);
-        const uint32_t ox0 = __shfl_sync(0xffffffffu, L.x0, own);
-        const int oy0 = (int)__shfl_sync(0xffffffffu, L.y0, own);
-        const int oy1 = (int)__shfl_sync(0xffffffffu, L.y1, own);
-        const TightBox ot = tight_box_of(L.tb, own);
-        if (e < items) {
-            int rlo, rhi;
-            const int k = tight_tile_rows(ot, (int)(ox0 + col) * TW, TW, TH, oy0, oy1, &rlo, &rhi);
-            if (k) atomicAdd(&cnt[wofs + own], (uint32_t)k);
-        }
-    }
-    __syncwarp();
-    if (valid) tiles_sorted[idx] = cnt[threadIdx.x];
+    const uint32_t c = warp_tight_count<TW, TH>(L, cnt + (threadIdx.x & ~31));
+    if (valid) tiles_sorted[idx] = c;
 }
 
 // Emission of the tight instances: entry e's instances fill exactly
@@ -417,13 +432,13 @@ __global__ void __launch_bounds__(256) count_tight(const uint32_t* order,
 template <int TW, int TH, typename KT>
 __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, const uint32_t* tiles_sorted,
                                                         const uint32_t* offsets, const uint4* rec,
-                                                        int64_t m, int64_t n, int64_t* status,
+                                                        int64_t m, const int64_t* mv, int64_t n, int64_t* status,
                                                         int64_t capacity, Views vs, KT* tkey,
                                                         uint32_t* tval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t wbase = idx - (threadIdx.x & 31);
     const int lane = threadIdx.x & 31;
-    const bool valid = idx < m;
+    const bool valid = idx < pass_count(mv, m);
     const bool fits = status[LGS_ST_NUM_INSTANCES] <= capacity;
     const uint32_t cnt = (valid && fits) ? tiles_sorted[idx] : 0u;
     const uint32_t incl = warp_inclusive_sum(cnt);
@@ -875,15 +890,33 @@ struct RsSmem {
     uint32_t ws[32];
     uint32_t start[RADIX];   // block-local start of each digit
     uint32_t base[RADIX];    // global output position of each digit's first element in this block
+    uint32_t tcnt[RS_THREADS];   // per-warp tight counters of the fused count
     KT keys[RS_TILE];
     uint32_t vals[RS_TILE];
 };
 
-template <typename KT>
+// What the last entry pass also does with LGS_FLAG_TIGHT (the tight count
+// folded into the pass): its sorted entries are the depth order, so it writes
+// their tight instance counts and depth-ordered emission records as it
+// scatters them, instead of a separate kernel reading the order back.
+struct RsTightCount {
+    const uint64_t* rect;
+    const float4* xy;
+    const float4* conic;
+    const uint4* emit;
+    Views vs;
+    int64_t n;
+    uint32_t* tiles_sorted;
+    uint4* rec;
+};
+
+// TW > 0: the scatter also runs the fused tight count (keys are not written).
+template <typename KT, int TW = 0, int TH = 0>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT* __restrict__ kout,
                                                               uint32_t* __restrict__ vout, const int64_t* cnt,
                                                               int64_t count, int shift, const uint32_t* offsets,
-                                                              int64_t nb, int64_t* err_status) {
+                                                              int64_t nb, int64_t* err_status,
+                                                              RsTightCount tc = RsTightCount{}) {
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;      // 512
     __shared__ RsSmem<KT> S;
@@ -950,14 +983,45 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
         }
     }
     __syncthreads();
+    if constexpr (TW == 0) {
 #pragma unroll 4
-    for (int j = t; j < (int)n_kept; j += RS_THREADS) {
-        const uint32_t key = S.keys[j];
-        const uint32_t d = (key >> shift) & 0xffu;
-        const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
-        if (LGS_CHECK((int64_t)gpos < K, 9, err_status)) {
-            kout[gpos] = (KT)key;
-            vout[gpos] = S.vals[j];
+        for (int j = t; j < (int)n_kept; j += RS_THREADS) {
+            const uint32_t key = S.keys[j];
+            const uint32_t d = (key >> shift) & 0xffu;
+            const uint32_t gpos = S.base[d] + (uint32_t)j - S.start[d];
+            if (LGS_CHECK((int64_t)gpos < K, 9, err_status)) {
+                kout[gpos] = (KT)key;
+                vout[gpos] = S.vals[j];
+            }
+        }
+    } else {
+        // every lane of a warp takes part in each round (the count is warp-cooperative)
+        for (int j0 = 0; j0 < (int)n_kept; j0 += RS_THREADS) {
+            const int j = j0 + t;
+            bool live = j < (int)n_kept;
+            uint32_t ent = 0u, gpos = 0u;
+            if (live) {
+                const uint32_t d = (S.keys[j] >> shift) & 0xffu;
+                gpos = S.base[d] + (uint32_t)j - S.start[d];
+                ent = S.vals[j];
+                live = LGS_CHECK((int64_t)gpos < K, 9, err_status);
+                if (live) vout[gpos] = ent;
+            }
+            TightLane L;
+            if (tc.emit) {
+                uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
+                if (live) {
+                    a = tc.emit[2 * (int64_t)ent];
+                    c = tc.emit[2 * (int64_t)ent + 1];
+                    tc.rec[2 * (int64_t)gpos] = a;
+                    tc.rec[2 * (int64_t)gpos + 1] = c;
+                }
+                L = tight_lane_from(ent, live, a, c, tc.vs, tc.n);
+            } else {
+                L = tight_lane_load(ent, live, tc.rect, tc.xy, tc.conic, tc.vs, tc.n, tc.rec, gpos);
+            }
+            const uint32_t c = warp_tight_count<TW, TH>(L, S.tcnt + (t & ~31));
+            if (live) tc.tiles_sorted[gpos] = c;
         }
     }
 }
@@ -1186,8 +1250,8 @@ static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
     uint32_t *va = (passes & 1) ? ws->bv : a.vals, *vb = (passes & 1) ? a.vals : ws->bv;
     if (a.tight) {
 #define LGS_EMIT_TIGHT(TW_, TH_)                                                                          \
-    emit_pairs_tight<TW_, TH_, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec, m, a.n, \
-                                                      a.d_status, capacity, *vs, ka, va)
+    emit_pairs_tight<TW_, TH_, KT><<<eg, 256, 0, s>>>(a.order, ws->tiles_s, ws->offsets, ws->erec, m, ws->mvis, \
+                                                      a.n, a.d_status, capacity, *vs, ka, va)
         const int tw = vs->tile_w, th = vs->tile_h;
         if (tw == 16 && th == 16) LGS_EMIT_TIGHT(16, 16);
         else if (tw == 8 && th == 32) LGS_EMIT_TIGHT(8, 32);
@@ -1256,25 +1320,49 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     onesweep_prepare(entries, nullptr, m, 4, ws->bases, ws->mvis, s);
     const bool os = (vs->flags & LGS_FLAG_ONESWEEP) != 0;
     radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s, os);
-    uint32_t *k0 = ws->ek2, *v0 = ws->ev2, *k1 = ws->ek, *v1 = ws->ev;
-    for (int shift = 8; shift < 32; shift += 8) {
-        radix_pass(OsSrc{k0, v0, nullptr, nullptr}, k1, v1, ws->mvis, m, shift,
-                   ws->bases + RADIX * (shift / 8), ws, d_status, s, os);
-        uint32_t* t = k0; k0 = k1; k1 = t;
-        t = v0; v0 = v1; v1 = t;
-    }
-    const uint32_t* order = v0;
-    // 2. scan of tiles-touched (with LGS_FLAG_TIGHT: of the tight counts) in depth order
     const bool tight = (vs->flags & LGS_FLAG_TIGHT) != 0;
     const float4* pxy = reinterpret_cast<const float4*>(pre->xy);
     const float4* pco = reinterpret_cast<const float4*>(pre->conic);
     const uint4* pem = reinterpret_cast<const uint4*>(pre->emit);
     const unsigned eg = (unsigned)ceil_div(m, 256);
+    // with tight emission and reduce-then-scan passes, the last entry pass
+    // also computes the tight counts (fused; no count kernel afterwards)
+    const bool fused = tight && !os;
+    uint32_t *k0 = ws->ek2, *v0 = ws->ev2, *k1 = ws->ek, *v1 = ws->ev;
+    for (int shift = 8; shift < 32; shift += 8) {
+        if (shift == 24 && fused) {
+            const int64_t nb = ceil_div(m, RS_TILE);
+            uint32_t* counts = reinterpret_cast<uint32_t*>(ws->look);
+            const RsSrc<uint32_t> rs{k0, v0, nullptr, nullptr};
+            const RsTightCount tc{pre->rect, pxy, pco, pem, *vs, n, ws->tiles_s, ws->erec};
+            rs_upsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, ws->mvis, m, shift, counts, nb);
+            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, ws->mvis, m, ws->bases + RADIX * 3);
+#define LGS_FUSED_PASS(TW_, TH_)                                                                             \
+    rs_downsweep<uint32_t, TW_, TH_><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, k1, v1, ws->mvis, m, shift, counts, nb, \
+                                                                         d_status, tc)
+            const int tw = vs->tile_w, th = vs->tile_h;
+            if (tw == 16 && th == 16) LGS_FUSED_PASS(16, 16);
+            else if (tw == 8 && th == 32) LGS_FUSED_PASS(8, 32);
+            else if (tw == 32 && th == 8) LGS_FUSED_PASS(32, 8);
+            else if (tw == 32 && th == 32) LGS_FUSED_PASS(32, 32);
+            else if (tw == 16 && th == 32) LGS_FUSED_PASS(16, 32);
+            else LGS_FUSED_PASS(32, 16);
+#undef LGS_FUSED_PASS
+        } else {
+            radix_pass(OsSrc{k0, v0, nullptr, nullptr}, k1, v1, ws->mvis, m, shift,
+                       ws->bases + RADIX * (shift / 8), ws, d_status, s, os);
+        }
+        uint32_t* t = k0; k0 = k1; k1 = t;
+        t = v0; v0 = v1; v1 = t;
+    }
+    const uint32_t* order = v0;
+    // 2. scan of tiles-touched (with LGS_FLAG_TIGHT: of the tight counts) in depth order
 #define LGS_COUNT_TIGHT(TW_, TH_)                                                                       \
     count_tight<TW_, TH_><<<eg, 256, 0, s>>>(order, pre->rect, pxy, pco, pem, m, ws->mvis, n, *vs, ws->tiles_s, \
                                              ws->erec)
     const int tw = vs->tile_w, th = vs->tile_h;
     if (!tight) gather_tiles<<<152 * 8, 256, 0, s>>>(order, pre->tiles, m, ws->mvis, ws->tiles_s);
+    else if (fused) {}
     else if (tw == 16 && th == 16) LGS_COUNT_TIGHT(16, 16);
     else if (tw == 8 && th == 32) LGS_COUNT_TIGHT(8, 32);
     else if (tw == 32 && th == 8) LGS_COUNT_TIGHT(32, 8);
@@ -1283,9 +1371,9 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     else LGS_COUNT_TIGHT(32, 16);
 #undef LGS_COUNT_TIGHT
     const int64_t nscan = ceil_div(m, SCAN_TILE);
-    scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums);
+    scan_reduce<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->mvis, ws->block_sums);
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, nscan, d_status, capacity);
-    scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->block_sums,
+    scan_downsweep<<<(unsigned)nscan, SCAN_THREADS, 0, s>>>(ws->tiles_s, m, ws->mvis, ws->block_sums,
                                                             ws->offsets);
     // 3-5: emission, tile-id passes and ranges, with u16 tile ids when the
     //      batch has at most 2^16 tiles (reduce-then-scan passes only)
