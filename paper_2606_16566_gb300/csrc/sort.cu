@@ -1327,7 +1327,11 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     const unsigned eg = (unsigned)ceil_div(m, 256);
     // with tight emission and reduce-then-scan passes, the last entry pass
     // also computes the tight counts (fused; no count kernel afterwards)
+#ifdef LGS_NO_FUSED_COUNT
+    const bool fused = false;
+#else
     const bool fused = tight && !os;
+#endif
     uint32_t *k0 = ws->ek2, *v0 = ws->ev2, *k1 = ws->ek, *v1 = ws->ev;
     for (int shift = 8; shift < 32; shift += 8) {
         if (shift == 24 && fused) {
