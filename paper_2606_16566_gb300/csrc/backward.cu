@@ -638,8 +638,11 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
     }
 }
 
+#ifndef LGS_PREBWD_MIN_BLOCKS
+#define LGS_PREBWD_MIN_BLOCKS 1
+#endif
 template <int DEG>
-__global__ void __launch_bounds__(128) preprocess_bwd(PreBwdParams p, Views vs) {
+__global__ void __launch_bounds__(128, LGS_PREBWD_MIN_BLOCKS) preprocess_bwd(PreBwdParams p, Views vs) {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n) return;

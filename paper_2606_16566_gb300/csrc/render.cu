@@ -100,24 +100,18 @@ __device__ __forceinline__ void write_pixel(const Views& vs, const RenderParams&
 }
 
 // ------------------------------------------------------------------ Local-GS
-// The 16-B records of a staged Gaussian sit at the same byte offset in every
-// row of rec, so a warp's list holds that offset and the blend loop addresses
-// all of them without index arithmetic. With one pixel per lane (NREC = 3):
-// (A, B, C, F), (D, E, -, -), (-r, -g, -b, p) in the log2 domain, colour
-// negated (see the blend), p = list position + 1 as bits. With two pixels per
-// lane (NREC = 5) every coefficient is stored twice, so that each half of a
-// packed two-wide instruction reads it from its own register:
-// (A, A, B, B), (C, C, F, F), (D, D, E, E), (-r, -r, -g, -g), (-b, -b, p, -).
-template <int NB, int NREC>
+// The three 16-B records of a staged Gaussian sit at the same byte offset in
+// sV, sDE and sC, so a warp's list holds that offset and the blend loop
+// addresses all three without index arithmetic.
+template <int NB>
 struct LocalSmem {
     float4 raw[2][3][NB];  // double-buffered cp.async landing zone: xy, conic, rgb records
-    float4 rec[NREC][NB];
+    float4 sV[NB];         // (A, B, C, F), log2 domain
+    float4 sDE[NB];        // (D, E, -, -)
+    float4 sC[NB];         // (-r, -g, -b, list position + 1 as bits): colour negated, see the blend
     uint8_t sM[NB];        // warp-block mask
     uint16_t sL[8][NB];    // per warp: byte offsets (16 x batch index) of its set mask bits, in order
 };
-
-template <int PPL>
-constexpr int kRecords = PPL == 2 ? 5 : 3;
 
 template <typename T>
 __device__ __forceinline__ const float4& at_offset(const T* base, int off) {
@@ -152,7 +146,7 @@ constexpr float INF_F = __builtin_huge_valf();
 // The region (CW x CH pixels at X0, Y0) walks the whole list of its tile.
 template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
 __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views& vs, uint32_t work,
-                                             LocalSmem<NB, kRecords<TileLayout<TW, TH, WX, WY>::PPL>>& S) {
+                                             LocalSmem<NB>& S) {
     using Reg = Regions<TW, TH>;
     constexpr int CW = Reg::CW, CH = Reg::CH;
     using Lay = Layout<CW, CH, WX, WY>;
@@ -250,20 +244,10 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                 const float Dn = fmaf(co.x, dx, co.y * dy);
                 const float En = fmaf(co.y, dx, co.z * dy);
                 const float Fn = -0.5f * fmaf(dx, Dn, dy * En);
-                const float A = -0.5f * LOG2E * co.x, B = -LOG2E * co.y, C = -0.5f * LOG2E * co.z;
-                const float F = fmaf(Fn, LOG2E, __log2f(co.w)), D = Dn * LOG2E, E = En * LOG2E;
-                const float pos = __uint_as_float(b0 + (uint32_t)sl + 1u);
-                if constexpr (PPL == 2) {
-                    S.rec[0][sl] = make_float4(A, A, B, B);
-                    S.rec[1][sl] = make_float4(C, C, F, F);
-                    S.rec[2][sl] = make_float4(D, D, E, E);
-                    S.rec[3][sl] = make_float4(-col.x, -col.x, -col.y, -col.y);
-                    S.rec[4][sl] = make_float4(-col.z, -col.z, pos, 0.f);
-                } else {
-                    S.rec[0][sl] = make_float4(A, B, C, F);
-                    S.rec[1][sl] = make_float4(D, E, 0.f, 0.f);
-                    S.rec[2][sl] = make_float4(-col.x, -col.y, -col.z, pos);
-                }
+                S.sV[sl] = make_float4(-0.5f * LOG2E * co.x, -LOG2E * co.y, -0.5f * LOG2E * co.z,
+                                       fmaf(Fn, LOG2E, __log2f(co.w)));
+                S.sDE[sl] = make_float4(Dn * LOG2E, En * LOG2E, 0.f, 0.f);
+                S.sC[sl] = make_float4(-col.x, -col.y, -col.z, __uint_as_float(b0 + (uint32_t)sl + 1u));
                 S.sM[sl] = (uint8_t)block_mask<CW, CH, WX, WY>(co.x, co.y, co.z, co.w, __fadd_rn(xy.x, xy.z),
                                                                __fadd_rn(xy.y, xy.w), X0, Y0);
             }
@@ -297,29 +281,12 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                         if (__all_sync(0xffffffffu, lane_done())) break;
                         ++pairs;
                     }
-                    // the Gaussian's coefficients and negated colour, each
-                    // as a value of the lane's PPL pixels
-                    P cA, cB, cC, cD, cE, cF, nr, ng, nbl;
-                    uint32_t idx;
-                    if constexpr (PPL == 2) {
-                        const float4 r0 = at_offset(S.rec[0], off), r1 = at_offset(S.rec[1], off);
-                        const float4 r2 = at_offset(S.rec[2], off), r3 = at_offset(S.rec[3], off);
-                        const float4 r4 = at_offset(S.rec[4], off);
-                        cA = {make_float2(r0.x, r0.y)}; cB = {make_float2(r0.z, r0.w)};
-                        cC = {make_float2(r1.x, r1.y)}; cF = {make_float2(r1.z, r1.w)};
-                        cD = {make_float2(r2.x, r2.y)}; cE = {make_float2(r2.z, r2.w)};
-                        nr = {make_float2(r3.x, r3.y)}; ng = {make_float2(r3.z, r3.w)};
-                        nbl = {make_float2(r4.x, r4.y)};
-                        idx = __float_as_uint(r4.z);
-                    } else {
-                        const float4 r0 = at_offset(S.rec[0], off), r1 = at_offset(S.rec[1], off);
-                        const float4 r2 = at_offset(S.rec[2], off);
-                        cA = bcast<PPL>(r0.x); cB = bcast<PPL>(r0.y); cC = bcast<PPL>(r0.z); cF = bcast<PPL>(r0.w);
-                        cD = bcast<PPL>(r1.x); cE = bcast<PPL>(r1.y);
-                        nr = bcast<PPL>(r2.x); ng = bcast<PPL>(r2.y); nbl = bcast<PPL>(r2.z);
-                        idx = __float_as_uint(r2.w);
-                    }
-                    const P pw = pfma(cA, bx2, pfma(cB, bxy, pfma(cC, by2, pfma(cD, bxl, pfma(cE, byl, cF)))));
+                    const float4 V = at_offset(S.sV, off);
+                    const float4 DE = at_offset(S.sDE, off);
+                    const float4 ncol = at_offset(S.sC, off);
+                    const uint32_t idx = __float_as_uint(ncol.w);
+                    const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
+                                 pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
                     // -alpha = -min(0.99, 2^pw), negated so that the packed
                     // updates below need no separate negation
                     P nal;
@@ -327,9 +294,9 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                     for (int k = 0; k < PPL; ++k) nal[k] = fmaxf(-0.99f, -ex2_approx(pw[k]));
                     if (VAR == VAR_LITERAL) {
                         const P nw = pmul(nal, T);          // -w = -alpha T
-                        C0 = pfma(nr, nw, C0);
-                        C1 = pfma(ng, nw, C1);
-                        C2 = pfma(nbl, nw, C2);
+                        C0 = pfma(bcast<PPL>(ncol.x), nw, C0);
+                        C1 = pfma(bcast<PPL>(ncol.y), nw, C1);
+                        C2 = pfma(bcast<PPL>(ncol.z), nw, C2);
                         T = padd(T, nw);                    // T - w
 #pragma unroll
                         for (int k = 0; k < PPL; ++k) last[k] = idx;
@@ -348,9 +315,9 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
                         last[k] = blend ? idx : last[k];
                     }
                     const P nw = pmul(nab, T);              // -w
-                    C0 = pfma(nr, nw, C0);                  // (-c)(-w) = c w exactly
-                    C1 = pfma(ng, nw, C1);
-                    C2 = pfma(nbl, nw, C2);
+                    C0 = pfma(bcast<PPL>(ncol.x), nw, C0);  // (-c)(-w) = c w exactly
+                    C1 = pfma(bcast<PPL>(ncol.y), nw, C1);
+                    C2 = pfma(bcast<PPL>(ncol.z), nw, C2);
                     T = pfma(nab, T, T);                    // T - alpha T, or T unchanged
                 }
                 if (__all_sync(0xffffffffu, lane_done())) warp_done = true;
@@ -382,7 +349,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
 // One CTA per (tile, region).
 template <int TW, int TH, int WX, int WY, bool COUNT, int VAR, int NB>
 __global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_localgs(RenderParams p, Views vs) {
-    __shared__ LocalSmem<NB, kRecords<TileLayout<TW, TH, WX, WY>::PPL>> S;
+    __shared__ LocalSmem<NB> S;
     localgs_tile<TW, TH, WX, WY, COUNT, VAR, NB>(p, vs, blockIdx.x, S);
 }
 
@@ -393,7 +360,7 @@ __global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_localgs
 template <int TW, int TH, int WX, int WY, bool COUNT, int NB>
 __global__ void __launch_bounds__(TileLayout<TW, TH, WX, WY>::NT) render_localgs_persistent(RenderParams p,
                                                                                          Views vs) {
-    __shared__ LocalSmem<NB, kRecords<TileLayout<TW, TH, WX, WY>::PPL>> S;
+    __shared__ LocalSmem<NB> S;
     __shared__ uint32_t s_work;
     unsigned long long* q = reinterpret_cast<unsigned long long*>(p.status + LGS_ST_QUEUE);
     const uint32_t n_work = vs.n_tiles * (uint32_t)Regions<TW, TH>::N;
