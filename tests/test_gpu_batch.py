@@ -80,8 +80,9 @@ def test_autotune_picks_a_measured_candidate(tmp_path):
     assert again["cached"] and tuple(again["tile"]) == tuple(res["tile"])
 
 
-@pytest.mark.parametrize("tile,persistent,tight", [((16, 16), True, False), ((8, 32), False, True)])
-def test_batched_64_uneven_views_graph_fwd_bwd(tile, persistent, tight):
+@pytest.mark.parametrize("tile,persistent,tight,block", [((16, 16), True, False, None), ((8, 32), False, True, None),
+                                                       ((32, 16), False, True, (8, 8))])
+def test_batched_64_uneven_views_graph_fwd_bwd(tile, persistent, tight, block):
     """The batched workload: 3M clustered SH3 Gaussians, 64 cameras of uneven
     resolution (800..1920 x 800..1080), forward + backward captured in one CUDA
     graph (view groups of at most 2^16 tiles); two views checked against the
@@ -90,7 +91,7 @@ def test_batched_64_uneven_views_graph_fwd_bwd(tile, persistent, tight):
     sc, cams = scenes.batched()
     assert len(cams) == 64
     g = lgs.to_device(sc)
-    r = batch.Renderer(g, cams, tile=tile, persistent=persistent, backward=True, tight=tight)
+    r = batch.Renderer(g, cams, tile=tile, persistent=persistent, backward=True, tight=tight, block=block)
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
     r.step()

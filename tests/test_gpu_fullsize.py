@@ -9,6 +9,7 @@ import torch
 
 import oracle
 from paper_2606_16566_gb300 import batch, lgs, scenes
+from paper_2606_16566_gb300 import _lib as L
 
 from parity import assert_image_parity, full_view_parity, sample_tiles, to_numpy_view
 
@@ -25,13 +26,15 @@ def _check_sampled(sc, cams, res, v, frac, seed, tile=(16, 16), tight=False):
     assert_image_parity(rep, f"view {v}")
 
 
-@pytest.mark.parametrize("tight", [False, True])
-def test_indoor_training_step(tight):
+@pytest.mark.parametrize("tight,tile,block", [(False, (16, 16), None), (True, (16, 16), None),
+                                              (True, (32, 32), (8, 8))])
+def test_indoor_training_step(tight, tile, block):
     """Forward + L1 loss against a seeded random target + full adjoint (the
-    benchmark's indoor step uses tight-box emission)."""
+    benchmark's indoor step uses tight-box emission and the autotuner's tile,
+    32x32 tiles rendered as 16x16 regions of 8x8 warp blocks on this scene)."""
     sc, cams = scenes.indoor()
     g = lgs.to_device(sc)
-    r = batch.Renderer(g, cams, backward=True, tight=tight)
+    r = batch.Renderer(g, cams, backward=True, tight=tight, tile=tile, block=block)
     r.forward()
     target = torch.rand(r.rgb.shape, generator=torch.Generator(device="cuda").manual_seed(7), device="cuda")
     loss = (r.rgb - target).abs().mean()
@@ -46,7 +49,7 @@ def test_indoor_training_step(tight):
     vals, ranges = r.lists()
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
            "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
-    _check_sampled(sc, cams, res, 0, 0.05, seed=11, tight=tight)
+    _check_sampled(sc, cams, res, 0, 0.05, seed=11, tight=tight, tile=tile)
 
 
 def _indoor_crop(n_keep=2000, win=128):
@@ -61,6 +64,26 @@ def _indoor_crop(n_keep=2000, win=128):
     keep = np.sort(vis[np.argsort(d)[:n_keep]])
     crop = {k: np.ascontiguousarray(v[keep]) for k, v in sc.items()}
     return crop, scenes.crop_camera(cam, x0, y0, win, win)
+
+
+def test_indoor_crop_gradients_large_tiles_vs_oracle():
+    """The indoor crop's gradients in the benchmark's indoor launch
+    configuration (32x32 tiles, 16x16 regions of 8x8 blocks, two pixels per
+    lane) against the oracle's FP64 adjoint on the same tiles."""
+    sc, cam = _indoor_crop()
+    H, W = cam["height"], cam["width"]
+    rng = np.random.default_rng(22)
+    g_rgb = rng.standard_normal((3, H, W)).astype(np.float32)
+    g = lgs.to_device(sc)
+    res = lgs.render(g, [cam], tile=(32, 32), flags=L.FLAG_TIGHT)
+    gr = lgs.render_bwd(g, [cam], res["cfg"], res["pre"], res["vals"], res["ranges"], res["T_flat"],
+                        res["nc_flat"], torch.from_numpy(g_rgb).cuda().reshape(-1))
+    ref = oracle.backward(sc, cam, g_rgb, None, 32, 32)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        got = gr[k].cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(got - ref[k]) / max(np.linalg.norm(ref[k]), 1e-30)
+        print(k, rel)
+        assert rel <= 1e-3, (k, rel)
 
 
 def test_indoor_crop_gradients_vs_oracle_and_fd():
@@ -129,14 +152,16 @@ def test_scale_30M_sampled_view():
     _check_sampled(sc, cams, res, 1, 0.04, seed=12)
 
 
-def test_scale_30M_bench_configuration():
+@pytest.mark.parametrize("tile,block,groups", [((16, 16), (8, 8), 2), ((32, 32), (8, 8), 1)])
+def test_scale_30M_bench_configuration(tile, block, groups):
     """The benchmark's scale configuration: all 16 views of 1920x1080 in one
-    Renderer with tight-box emission (two view groups of 8); two views, one
-    per group, checked on sampled tiles."""
+    Renderer with tight-box emission (the tight count fused into the last
+    entry pass at this size); 16x16 tiles in two view groups of 8, or 32x32
+    tiles in one group; two views checked on sampled tiles."""
     sc, cams = scenes.scale()
     g = lgs.to_device(sc)
-    r = batch.Renderer(g, cams, tight=True)
-    assert len(r.groups) == 2
+    r = batch.Renderer(g, cams, tight=True, tile=tile, block=block)
+    assert len(r.groups) == groups
     r.forward()
     torch.cuda.synchronize()
     r.check()
@@ -144,4 +169,4 @@ def test_scale_30M_bench_configuration():
     res = {"rgb": r.images(), "final_T": lgs.split_views(r.T, cams, 0),
            "n_contrib": lgs.split_views(r.nc, cams, 0), "vals": vals, "ranges": ranges}
     for v, seed in ((5, 13), (12, 14)):
-        _check_sampled(sc, cams, res, v, 0.02, seed=seed, tight=True)
+        _check_sampled(sc, cams, res, v, 0.02, seed=seed, tight=True, tile=tile)
