@@ -911,7 +911,36 @@ struct RsTightCount {
 };
 
 // TW > 0: the scatter also runs the fused tight count (keys are not written).
-template <typename KT, int TW = 0, int TH = 0>
+// Stable rank of each of a warp's RS_ITEMS x 32 digits (item i of lane l is
+// element i * 32 + l of the warp's range) among equal digits, with the warp's
+// counters cnt advanced: one ballot per significant digit bit (NBITS: the
+// digits of the pass are known to be < 2^NBITS), plus one for the kept bit
+// when some element of the warp is dropped (d = 0x100).
+template <int NBITS, bool WITH_DROP>
+__device__ __forceinline__ void warp_rank(const uint32_t (&d)[RS_ITEMS], uint32_t* cnt, uint16_t (&rk)[RS_ITEMS]) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < NBITS; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d[i] >> b) & 1u);
+            peers &= ((d[i] >> b) & 1u) ? bal : ~bal;
+        }
+        if (WITH_DROP) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, d[i] >> 8);
+            peers &= (d[i] >> 8) ? bal : ~bal;
+        }
+        const uint32_t b = d[i] < 0x100u ? cnt[d[i]] : 0u;
+        rk[i] = (uint16_t)(b + __popc(peers & lt));
+        __syncwarp();
+        if (d[i] < 0x100u && (peers >> lane) == 1u) cnt[d[i]] = b + __popc(peers);
+        __syncwarp();
+    }
+}
+
+template <typename KT, int TW = 0, int TH = 0, int NBITS = 8>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT* __restrict__ kout,
                                                               uint32_t* __restrict__ vout, const int64_t* cnt,
                                                               int64_t count, int shift, const uint32_t* offsets,
@@ -921,7 +950,6 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
     constexpr int PER_WARP = RS_TILE / NW;      // 512
     __shared__ RsSmem<KT> S;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t lt = lanemask_lt();
     const int64_t K = pass_count(cnt, count);
     const int64_t first = (int64_t)blockIdx.x * RS_TILE;
     if (first >= K) return;
@@ -945,21 +973,13 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
     // stable rank of every kept key among equal digits of its warp's range
     // (one ballot per digit bit; bit 8 marks a dropped element)
     uint16_t rk[RS_ITEMS];
+    uint32_t dg[RS_ITEMS];
 #pragma unroll
-    for (int i = 0; i < RS_ITEMS; ++i) {
-        const uint32_t d = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
-        uint32_t peers = 0xffffffffu;
-#pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bal : ~bal;
-        }
-        const uint32_t b = d < 0x100u ? S.cnt[warp][d] : 0u;
-        rk[i] = (uint16_t)(b + __popc(peers & lt));
-        __syncwarp();
-        if (d < 0x100u && (peers >> lane) == 1u) S.cnt[warp][d] = b + __popc(peers);
-        __syncwarp();
-    }
+    for (int i = 0; i < RS_ITEMS; ++i) dg[i] = (keep & (1u << i)) ? ((k[i] >> shift) & 0xffu) : 0x100u;
+    if (__all_sync(0xffffffffu, keep == (1u << RS_ITEMS) - 1u))
+        warp_rank<NBITS, false>(dg, S.cnt[warp], rk);
+    else
+        warp_rank<NBITS, true>(dg, S.cnt[warp], rk);
     __syncthreads();
     uint32_t pre[NW], acc = 0;
 #pragma unroll
@@ -1192,7 +1212,7 @@ static void onesweep_prepare(const OsSrc& src, const int64_t* cnt, int64_t count
 // table reuses the look-back words' space, which no concurrent pass uses).
 static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const int64_t* cnt,
                        int64_t count, int shift, const uint32_t* bases, const SortWs* ws,
-                       int64_t* d_status, cudaStream_t s, bool onesweep) {
+                       int64_t* d_status, cudaStream_t s, bool onesweep, int nbits = 8) {
     if (onesweep) {
         const int64_t nt = ceil_div(count, OS_TILE);
         if (nt == 0) return;
@@ -1208,8 +1228,12 @@ static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const i
     const RsSrc<uint32_t> rs{src.k, src.v, src.tiles, src.depth};
     rs_upsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, cnt, count, shift, counts, nb);
     rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, cnt, count, bases);
-    rs_downsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift, counts, nb,
-                                                               d_status);
+    if (nbits <= 7)
+        rs_downsweep<uint32_t, 0, 0, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift,
+                                                                          counts, nb, d_status);
+    else
+        rs_downsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift, counts, nb,
+                                                                   d_status);
 }
 
 }  // namespace lgs
@@ -1271,18 +1295,26 @@ static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
         key_histogram<KT><<<152 * 4, 256, 0, s>>>(ka, kcount, capacity, passes, tbases);
         onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
     }
+    int tile_bits = 0;
+    while ((1u << tile_bits) < vs->n_tiles) ++tile_bits;
     for (int p = 0; p < passes; ++p) {
+        // significant bits of this pass's digit (tile ids are < n_tiles)
+        const int nbits = tile_bits - 8 * p < 8 ? tile_bits - 8 * p : 8;
         if constexpr (sizeof(KT) == 4) {
             radix_pass(OsSrc{ka, va, nullptr, nullptr}, kb, vb, kcount, capacity, 8 * p, tbases + p * RADIX, ws,
-                       a.d_status, s, a.onesweep);
+                       a.d_status, s, a.onesweep, nbits);
         } else {
             const int64_t nb = ceil_div(capacity, RS_TILE);
             uint32_t* counts = reinterpret_cast<uint32_t*>(ws->look);
             const RsSrc<KT> rs{ka, va, nullptr, nullptr};
             rs_upsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kcount, capacity, 8 * p, counts, nb);
             rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, kcount, capacity, tbases + p * RADIX);
-            rs_downsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p, counts, nb,
-                                                                 a.d_status);
+            if (nbits <= 7)
+                rs_downsweep<KT, 0, 0, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p,
+                                                                              counts, nb, a.d_status);
+            else
+                rs_downsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p, counts,
+                                                                     nb, a.d_status);
         }
         KT* t = ka; ka = kb; kb = t;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -1342,9 +1374,9 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
             const RsTightCount tc{pre->rect, pxy, pco, pem, *vs, n, ws->tiles_s, ws->erec};
             rs_upsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, ws->mvis, m, shift, counts, nb);
             rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, ws->mvis, m, ws->bases + RADIX * 3);
-#define LGS_FUSED_PASS(TW_, TH_)                                                                             \
-    rs_downsweep<uint32_t, TW_, TH_><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, k1, v1, ws->mvis, m, shift, counts, nb, \
-                                                                         d_status, tc)
+#define LGS_FUSED_PASS(TW_, TH_)                                                                          \
+    rs_downsweep<uint32_t, TW_, TH_, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, k1, v1, ws->mvis, m, shift, counts, \
+                                                                            nb, d_status, tc)
             const int tw = vs->tile_w, th = vs->tile_h;
             if (tw == 16 && th == 16) LGS_FUSED_PASS(16, 16);
             else if (tw == 8 && th == 32) LGS_FUSED_PASS(8, 32);
@@ -1354,8 +1386,9 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
             else LGS_FUSED_PASS(32, 16);
 #undef LGS_FUSED_PASS
         } else {
+            // the kept depths are positive floats: bit 31 of their keys is 0
             radix_pass(OsSrc{k0, v0, nullptr, nullptr}, k1, v1, ws->mvis, m, shift,
-                       ws->bases + RADIX * (shift / 8), ws, d_status, s, os);
+                       ws->bases + RADIX * (shift / 8), ws, d_status, s, os, shift == 24 ? 7 : 8);
         }
         uint32_t* t = k0; k0 = k1; k1 = t;
         t = v0; v0 = v1; v1 = t;
