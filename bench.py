@@ -423,26 +423,17 @@ def run_indoor(dev, steps):
     return out
 
 
-def run_scale(dev, steps, tile=(16, 16), block=None):
-    """The scale scene: 30M SH3 Gaussians (256 clusters + background), 16 views
-    of 1920x1080 in one batch (view groups of at most 2^16 tiles); forward with
-    per-stage events, forward+backward
-    as one graph replay, the warp-culled fraction of the Local-GS schedule, and
-    the HBM rate of preprocess (algorithmic bytes: 236 B read per Gaussian,
-    69 B written per (view, Gaussian) entry)."""
+# tile shapes timed on the scale scene (8x8 warp blocks, batch 128): the
+# larger tiles fit all 16 views in one view group of at most 2^16 tiles
+SCALE_TILES = ((16, 16), (32, 16), (32, 32))
+
+
+def _stage_times(r, flush, n):
+    """Median per-stage (preprocess, sort, render) forward times of `n` eager
+    steps after one warm-up, L2 flushed before each."""
     import torch
-    from paper_2606_16566_gb300 import batch, lgs, scenes
-    from paper_2606_16566_gb300 import _lib as L
-    sc, cams = scenes.scale()
-    g = lgs.to_device(sc, dev)
-    del sc
-    n, V = g["means"].shape[0], len(cams)
-    r = batch.Renderer(g, cams, tile=tile, backward=True, tight=True, block=block)
-    r.forward()
-    pairs, cands = r.count_pairs()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stage = []
-    for i in range(max(3, steps // 8) + 1):
+    for i in range(n + 1):
         flush.zero_()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
@@ -455,9 +446,44 @@ def run_scale(dev, steps, tile=(16, 16), block=None):
         torch.cuda.synchronize()
         if i >= 1:
             stage.append([e[k].elapsed_time(e[k + 1]) for k in range(3)])
+    return np.median(np.array(stage), 0)
+
+
+def run_scale(dev, steps, tile=None, block=None):
+    """The scale scene: 30M SH3 Gaussians (256 clusters + background), 16 views
+    of 1920x1080 in one batch (view groups of at most 2^16 tiles); forward with
+    per-stage events, forward+backward
+    as one graph replay, the warp-culled fraction of the Local-GS schedule, and
+    the HBM rate of preprocess (algorithmic bytes: 236 B read per Gaussian,
+    69 B written per (view, Gaussian) entry). Without a fixed tile the forward
+    of each shape in SCALE_TILES is timed and the fastest measured."""
+    import torch
+    from paper_2606_16566_gb300 import batch, lgs, scenes
+    from paper_2606_16566_gb300 import _lib as L
+    sc, cams = scenes.scale()
+    g = lgs.to_device(sc, dev)
+    del sc
+    n, V = g["means"].shape[0], len(cams)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tuned = None
+    if tile is None:
+        tuned = {}
+        for t in SCALE_TILES:
+            r = batch.Renderer(g, cams, tile=t, tight=True, block=(8, 8), batch=128)
+            r.forward()
+            tuned[f"{t[0]}x{t[1]}"] = float(_stage_times(r, flush, 2).sum())
+            del r
+            torch.cuda.empty_cache()
+        best = min(tuned, key=tuned.get)
+        tile, block, bsz = tuple(int(x) for x in best.split("x")), (8, 8), 128
+    else:
+        bsz = 0
+    r = batch.Renderer(g, cams, tile=tile, backward=True, tight=True, block=block, batch=bsz)
+    r.forward()
+    pairs, cands = r.count_pairs()
+    sm = _stage_times(r, flush, max(3, steps // 8))
     st = r.check()
     K = int(st[L.ST_NUM_INSTANCES])
-    sm = np.median(np.array(stage), 0)
     ms_f = float(sm.sum())
     r.d_rgb.fill_(1.0 / r.d_rgb.numel())
     r.capture()
@@ -466,7 +492,9 @@ def run_scale(dev, steps, tile=(16, 16), block=None):
     P = lgs.n_pixels(cams)
     pre_bytes = n * 236 + n * V * 69
     out = {"workload": "scale-30M-sh3-16x1920x1080 (tight)", "tile": list(tile),
-           "warp_block": list(block) if block else None, "frames_s": V / (ms_f * 1e-3),
+           "warp_block": list(block) if block else None, "staging_batch": bsz or 256,
+           "tile_choice": {"forward_ms_by_tile": tuned} if tuned else "fixed",
+           "frames_s": V / (ms_f * 1e-3),
            "mpix_s": P / 1e6 / (ms_f * 1e-3), "ms_per_step": ms_f,
            "stage_ms": {"preprocess": float(sm[0]), "sort": float(sm[1]), "render": float(sm[2])},
            "fwd_bwd": {"frames_s": V / (ms_fb * 1e-3), "ms_per_step": ms_fb, "replays": nrep},
@@ -553,7 +581,7 @@ def run_ours(args, rank, world):
     TF = L.FLAG_TIGHT
     tuned = None
     persistent = 0
-    nbat = 0
+    nbat = args.batch
     if args.tile == "auto":
         # tile shape, warp-block layout, staging batch and launch of the
         # Local-GS forward from the project's autotuner (timed graph replays of
@@ -724,7 +752,8 @@ def run_ours(args, rank, world):
     if not args.no_batched:
         batched, n_batched = run_batched(dev, args.steps)
     indoor = None if args.no_indoor else run_indoor(dev, args.steps)
-    scale = None if args.no_scale else run_scale(dev, args.steps, tile, block)
+    scale = None if args.no_scale else (run_scale(dev, args.steps) if args.tile == "auto"
+                                        else run_scale(dev, args.steps, tile, block))
     if rank != 0:
         return
     emission = "tight" if head.endswith("tight") else "rect"

@@ -305,47 +305,59 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
             }
             __syncwarp();
             int ns = 0;   // rows of the warp's buffer in use
-#pragma unroll 1
-            for (int i = nl - 1; i >= 0; --i) {
-                const int off = sLw[i];
-                const float4 V = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sV) + off);
-                const float4 DE = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sDE) + off);
-                const float4 col = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sC) + off);
-                const uint32_t pos = __float_as_uint(col.w);
+            // The T-independent front of a step (record loads, exponent,
+            // alpha, 1/(1 - alpha), the contribution predicates) of list
+            // entry i; the walk takes entries two at a time so that the front
+            // of the second overlaps the dependent updates of the first.
+            struct Front {
+                float4 col;
+                P nal, inv;
+                bool contrib[PPL], clamp[PPL];
+                int off;
+                bool any;
+            };
+            auto front = [&](int i) {
+                Front f;
+                f.off = sLw[i];
+                const float4 V = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sV) + f.off);
+                const float4 DE = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sDE) + f.off);
+                f.col = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(S.sC) + f.off);
+                const uint32_t pos = __float_as_uint(f.col.w);
                 const P pw = pfma(bcast<PPL>(V.x), bx2, pfma(bcast<PPL>(V.y), bxy, pfma(bcast<PPL>(V.z), by2,
                              pfma(bcast<PPL>(DE.x), bxl, pfma(bcast<PPL>(DE.y), byl, bcast<PPL>(V.w))))));
-                bool contrib[PPL];
-                bool any = false;
+                f.any = false;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
-                    contrib[k] = pos <= last[k] && pw[k] >= LOG2_ALPHA_MIN_B;
-                    any = any || contrib[k];
+                    f.contrib[k] = pos <= last[k] && pw[k] >= LOG2_ALPHA_MIN_B;
+                    f.any = f.any || f.contrib[k];
+                    // branch-free: pixels that do not contribute get alpha 0,
+                    // which leaves T and the colour behind exactly as they
+                    // were. Carried negated: nal = -alpha
+                    const float e2 = ex2_approx_b(pw[k]);
+                    f.clamp[k] = e2 > 0.99f;
+                    const float nal = fmaxf(-0.99f, -e2);
+                    f.inv[k] = __fdividef(1.f, 1.f + nal);  // 1 - alpha >= 0.01
+                    f.nal[k] = nal;
                 }
-                if (!__any_sync(0xffffffffu, any)) continue;   // nothing to reduce
-                // branch-free: pixels that do not contribute get alpha 0, which
-                // leaves T and the colour behind exactly as they were. Carried
-                // negated: nal = -alpha, nac = -alpha of a contributing pixel
-                P e2, nal, inv, nac;
+                return f;
+            };
+            auto apply = [&](const Front& f) {
+                P nac;
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    e2[k] = ex2_approx_b(pw[k]);
-                    nal[k] = fmaxf(-0.99f, -e2[k]);
-                    inv[k] = __fdividef(1.f, 1.f + nal[k]);  // 1 - alpha >= 0.01
-                    nac[k] = contrib[k] ? nal[k] : 0.f;
-                }
-                const P Tk = pmul(T, inv);
+                for (int k = 0; k < PPL; ++k) nac[k] = f.contrib[k] ? f.nal[k] : 0.f;
+                const P Tk = pmul(T, f.inv);
                 const P nw = pmul(nac, Tk);                  // -w = -alpha T
                 // <rgb_k - A_k, g>, and A <- alpha rgb + (1 - alpha) A carried as -<A, g>
-                const P cg = pfma(bcast<PPL>(col.z), g2, pfma(bcast<PPL>(col.y), g1,
-                                                               pfma(bcast<PPL>(col.x), g0, nAg)));
-                const P dal = pfma(ntail, inv, pmul(Tk, cg));  // dL/dalpha
+                const P cg = pfma(bcast<PPL>(f.col.z), g2, pfma(bcast<PPL>(f.col.y), g1,
+                                                                 pfma(bcast<PPL>(f.col.x), g0, nAg)));
+                const P dal = pfma(ntail, f.inv, pmul(Tk, cg));  // dL/dalpha
                 nAg = pfma(nac, cg, nAg);
-                const P ndal = pmul(dal, nal);               // -dL/dalpha alpha
+                const P ndal = pmul(dal, f.nal);             // -dL/dalpha alpha
                 float ndp[2] = {0.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
-                    T[k] = contrib[k] ? Tk[k] : T[k];
-                    ndp[k] = (contrib[k] && !(e2[k] > 0.99f)) ? ndal[k] : 0.f;
+                    T[k] = f.contrib[k] ? Tk[k] : T[k];
+                    ndp[k] = (f.contrib[k] && !f.clamp[k]) ? ndal[k] : 0.f;
                 }
                 // the lane's colour sums over its pixels (negated, like dp)
                 const P wg0 = pmul(nw, g0), wg1 = pmul(nw, g1), wg2 = pmul(nw, g2);
@@ -358,13 +370,24 @@ __device__ __forceinline__ void bwd_tile(const BwdParams& p, const Views& vs, ui
                 const int cc = lane ^ (ns & 7);
                 R.R4[ns][cc] = make_float4(ndp[0], ndp[1], W0, W1);
                 R.R1[ns][cc] = W2;
-                if (lane == 0) R.slot[ns] = (uint32_t)(off >> 4);
+                if (lane == 0) R.slot[ns] = (uint32_t)(f.off >> 4);
                 if (++ns == RED_ROWS) {
                     __syncwarp();
                     reduce_rows<CW, CH, WX, WY>(R, ns, S.sG, lane, warp);
                     __syncwarp();
                     ns = 0;
                 }
+            };
+#pragma unroll 1
+            for (int i = nl - 1; i >= 1; i -= 2) {
+                const Front fa = front(i);
+                const Front fb = front(i - 1);
+                if (__any_sync(0xffffffffu, fa.any)) apply(fa);   // else nothing to reduce
+                if (__any_sync(0xffffffffu, fb.any)) apply(fb);
+            }
+            if (nl & 1) {
+                const Front fa = front(0);
+                if (__any_sync(0xffffffffu, fa.any)) apply(fa);
             }
             if (ns > 0) {
                 __syncwarp();

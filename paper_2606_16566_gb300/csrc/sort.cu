@@ -865,15 +865,16 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(RsSrc<KT> src, const in
     }
 }
 
-// Row d of the count table -> exclusive prefix along the live blocks + the
-// digit's base (one CTA per digit).
+// Row d of the count table -> exclusive prefix along the live blocks, and the
+// row's total (the pass's count of digit d) into totals[d] (one CTA per digit).
+// rs_downsweep adds the digit's base, the exclusive prefix of the totals.
 __global__ void __launch_bounds__(1024) rs_scan(uint32_t* counts, int64_t nb, const int64_t* cnt, int64_t count,
-                                               const uint32_t* bases) {
+                                               uint32_t* totals) {
     __shared__ uint32_t ws[32];
     const int64_t K = pass_count(cnt, count);
     const int64_t live = ceil_div_dev(K, RS_TILE);
     uint32_t* row = counts + (int64_t)blockIdx.x * nb;
-    uint32_t carry = bases[blockIdx.x];
+    uint32_t carry = 0u;
     for (int64_t b0 = 0; b0 < live; b0 += 1024) {
         const int64_t b = b0 + threadIdx.x;
         const uint32_t v = b < live ? row[b] : 0u;
@@ -882,6 +883,7 @@ __global__ void __launch_bounds__(1024) rs_scan(uint32_t* counts, int64_t nb, co
         if (b < live) row[b] = carry + ex;
         carry += tot;
     }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 template <typename KT>
@@ -940,12 +942,16 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&d)[RS_ITEMS], uint32_
     }
 }
 
+// `totals`: the pass's digit counts from rs_scan; with `kept`, block 0 also
+// stores their sum, the number of elements the pass kept.
 template <typename KT, int TW = 0, int TH = 0, int NBITS = 8>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT* __restrict__ kout,
                                                               uint32_t* __restrict__ vout, const int64_t* cnt,
                                                               int64_t count, int shift, const uint32_t* offsets,
-                                                              int64_t nb, int64_t* err_status,
+                                                              const uint32_t* totals, int64_t nb,
+                                                              int64_t* err_status, int64_t* kept = nullptr,
                                                               RsTightCount tc = RsTightCount{}) {
+    static_assert(RS_THREADS == RADIX, "one thread per digit");
     constexpr int NW = RS_THREADS / 32;
     constexpr int PER_WARP = RS_TILE / NW;      // 512
     __shared__ RsSmem<KT> S;
@@ -954,7 +960,14 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(RsSrc<KT> src, KT*
     const int64_t first = (int64_t)blockIdx.x * RS_TILE;
     if (first >= K) return;
     for (int d = lane; d < RADIX; d += 32) S.cnt[warp][d] = 0;
-    S.base[t] = offsets[(int64_t)t * nb + blockIdx.x];
+    {
+        // global position of this block's first element of digit t: the
+        // digit's base (exclusive prefix of the totals) + the row prefix
+        uint32_t all;
+        const uint32_t dbase = block_exclusive_scan<RS_THREADS>(totals[t], S.ws, all);
+        S.base[t] = dbase + offsets[(int64_t)t * nb + blockIdx.x];
+        if (kept && blockIdx.x == 0 && t == 0) *kept = (int64_t)all;
+    }
     const int n_valid = (int)min((int64_t)RS_TILE, K - first);
     // keys first; the values are loaded only once their slots are known, so
     // they hold no registers through the ranking
@@ -1207,12 +1220,15 @@ static void onesweep_prepare(const OsSrc& src, const int64_t* cnt, int64_t count
 
 // One stable LSD pass over u32 keys carrying u32 values (element count from
 // the device word `cnt` when given, else `count`; the grid covers `count`).
-// With `onesweep` one look-back kernel (onesweep_pass), else the three
-// reduce-then-scan kernels (rs_upsweep, rs_scan, rs_downsweep; their count
-// table reuses the look-back words' space, which no concurrent pass uses).
+// With `onesweep` one look-back kernel (onesweep_pass; `bases` holds the
+// pass's digit bases from onesweep_prepare), else the three reduce-then-scan
+// kernels (rs_upsweep, rs_scan, rs_downsweep; `bases` is their 256-word digit
+// total scratch, their count table reuses the look-back words' space, which no
+// concurrent pass uses, and `kept`, when given, receives the kept count).
 static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const int64_t* cnt,
-                       int64_t count, int shift, const uint32_t* bases, const SortWs* ws,
-                       int64_t* d_status, cudaStream_t s, bool onesweep, int nbits = 8) {
+                       int64_t count, int shift, uint32_t* bases, const SortWs* ws,
+                       int64_t* d_status, cudaStream_t s, bool onesweep, int nbits = 8,
+                       int64_t* kept = nullptr) {
     if (onesweep) {
         const int64_t nt = ceil_div(count, OS_TILE);
         if (nt == 0) return;
@@ -1230,10 +1246,10 @@ static void radix_pass(const OsSrc& src, uint32_t* kout, uint32_t* vout, const i
     rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, cnt, count, bases);
     if (nbits <= 7)
         rs_downsweep<uint32_t, 0, 0, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift,
-                                                                          counts, nb, d_status);
+                                                                          counts, bases, nb, d_status, kept);
     else
-        rs_downsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift, counts, nb,
-                                                                   d_status);
+        rs_downsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kout, vout, cnt, count, shift, counts,
+                                                                   bases, nb, d_status, kept);
 }
 
 }  // namespace lgs
@@ -1290,7 +1306,9 @@ static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
     }
     const int64_t* kcount = a.d_status + LGS_ST_NUM_INSTANCES;
     uint32_t* tbases = ws->bases + OS_MAX_DIGITS * RADIX;
-    if (passes > 0) {
+    if (passes > 0 && a.onesweep) {
+        // digit bases of the look-back passes; the reduce-then-scan passes
+        // take their digit totals from their own count tables
         cudaMemsetAsync(tbases, 0, sizeof(uint32_t) * RADIX * passes, s);
         key_histogram<KT><<<152 * 4, 256, 0, s>>>(ka, kcount, capacity, passes, tbases);
         onesweep_bases<<<passes, RADIX, 0, s>>>(tbases);
@@ -1308,13 +1326,14 @@ static void tile_stage(const SortTileArgs& a, cudaStream_t s) {
             uint32_t* counts = reinterpret_cast<uint32_t*>(ws->look);
             const RsSrc<KT> rs{ka, va, nullptr, nullptr};
             rs_upsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kcount, capacity, 8 * p, counts, nb);
-            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, kcount, capacity, tbases + p * RADIX);
+            uint32_t* tot = tbases + p * RADIX;
+            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, kcount, capacity, tot);
             if (nbits <= 7)
                 rs_downsweep<KT, 0, 0, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p,
-                                                                              counts, nb, a.d_status);
+                                                                              counts, tot, nb, a.d_status);
             else
                 rs_downsweep<KT><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, kb, vb, kcount, capacity, 8 * p, counts,
-                                                                     nb, a.d_status);
+                                                                     tot, nb, a.d_status);
         }
         KT* t = ka; ka = kb; kb = t;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -1349,9 +1368,13 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
     // 1. visible entries by depth: the first pass forms (depth bits, entry)
     //    from tiles-touched and depth and drops the culled entries
     const OsSrc entries{nullptr, nullptr, pre->tiles, pre->depth};
-    onesweep_prepare(entries, nullptr, m, 4, ws->bases, ws->mvis, s);
     const bool os = (vs->flags & LGS_FLAG_ONESWEEP) != 0;
-    radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s, os);
+    // the look-back passes need every pass's digit bases (and the kept count)
+    // up front; the reduce-then-scan passes count their own digits, and the
+    // first one stores the kept count
+    if (os) onesweep_prepare(entries, nullptr, m, 4, ws->bases, ws->mvis, s);
+    radix_pass(entries, ws->ek2, ws->ev2, nullptr, m, 0, ws->bases, ws, d_status, s, os, 8,
+               os ? nullptr : ws->mvis);
     const bool tight = (vs->flags & LGS_FLAG_TIGHT) != 0;
     const float4* pxy = reinterpret_cast<const float4*>(pre->xy);
     const float4* pco = reinterpret_cast<const float4*>(pre->conic);
@@ -1373,10 +1396,11 @@ static lgs_status sort_enqueue(const lgs_pre_out* pre, int64_t n, const Views* v
             const RsSrc<uint32_t> rs{k0, v0, nullptr, nullptr};
             const RsTightCount tc{pre->rect, pxy, pco, pem, *vs, n, ws->tiles_s, ws->erec};
             rs_upsweep<uint32_t><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, ws->mvis, m, shift, counts, nb);
-            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, ws->mvis, m, ws->bases + RADIX * 3);
+            uint32_t* tot = ws->bases + RADIX * 3;
+            rs_scan<<<RADIX, 1024, 0, s>>>(counts, nb, ws->mvis, m, tot);
 #define LGS_FUSED_PASS(TW_, TH_)                                                                          \
     rs_downsweep<uint32_t, TW_, TH_, 7><<<(unsigned)nb, RS_THREADS, 0, s>>>(rs, k1, v1, ws->mvis, m, shift, counts, \
-                                                                            nb, d_status, tc)
+                                                                            tot, nb, d_status, nullptr, tc)
             const int tw = vs->tile_w, th = vs->tile_h;
             if (tw == 16 && th == 16) LGS_FUSED_PASS(16, 16);
             else if (tw == 8 && th == 32) LGS_FUSED_PASS(8, 32);
