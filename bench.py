@@ -742,8 +742,24 @@ def run_ours(args, rank, world):
             if st[L.ST_CODE] != 0:
                 raise L.LgsError(int(st[L.ST_CODE]), "device status in the end-to-end steps")
         ms_e2e = reduce_max_over_ranks([ms_e2e], world, dev)[0]
+        # the copies alone (same tensors, same streams, nothing overlapping):
+        # the end-to-end step is bound by max(device step, upload, download)
+        copy_ms = {}
+        for name, fn, strm in (("h2d", lambda: [gs[0][k].copy_(host[k], non_blocking=True) for k in gs[0]], s_in),
+                               ("d2h", lambda: out_h[0].copy_(pipes[0].rgb, non_blocking=True), s_out)):
+            with torch.cuda.stream(strm):
+                fn()
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(strm)
+                for _ in range(5):
+                    fn()
+                c1.record(strm)
+            torch.cuda.synchronize()
+            copy_ms[name] = c0.elapsed_time(c1) / 5
         e2e = {"value": world * views / (ms_e2e * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "copy_alone_ms": copy_ms,
+               "copy_alone_gbs": {"h2d": h2d / (copy_ms["h2d"] * 1e6), "d2h": d2h / (copy_ms["d2h"] * 1e6)},
                "schedule": "2 buffer sets, upload / render / download of consecutive steps on 3 streams"}
         del pipes[1], gs[1]
 

@@ -692,13 +692,19 @@ __global__ void __launch_bounds__(128, LGS_PREBWD_MIN_BLOCKS) preprocess_bwd(Pre
         if (p.tiles[m] == 0) continue;
         any = true;
         const ViewRec& c = vs.v[v];
-        const float gu = p.g_xy[2 * m], gv = p.g_xy[2 * m + 1];
-        const float ga = p.g_conic[4 * m], gbq = p.g_conic[4 * m + 1], gc = p.g_conic[4 * m + 2];
-        dop += p.g_conic[4 * m + 3];
+        // the per-entry scratch gradients: xy2d rows 8-B aligned, conic2d and
+        // rgb2d rows 16-B aligned (checked on the host)
+        const float2 gxy = reinterpret_cast<const float2*>(p.g_xy)[m];
+        const float4 gco = reinterpret_cast<const float4*>(p.g_conic)[m];
+        const float4 grgb = reinterpret_cast<const float4*>(p.g_rgb)[m];
+        const float gu = gxy.x, gv = gxy.y;
+        const float ga = gco.x, gbq = gco.y, gc = gco.z;
+        dop += gco.w;
         const uint8_t fl = p.flags[m];
         // ---- colour
         {
-            float gcol[3] = {p.g_rgb[4 * m], p.g_rgb[4 * m + 1], p.g_rgb[4 * m + 2]};
+            // a channel clamped at 0 in the forward passes no gradient
+            const float gm[3] = {(fl & 1u) ? 0.f : grgb.x, (fl & 2u) ? 0.f : grgb.y, (fl & 4u) ? 0.f : grgb.z};
             float d0 = mx - c.campos[0], d1 = my - c.campos[1], d2 = mz - c.campos[2];
             const float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
             const float id = 1.f / dn;
@@ -707,18 +713,31 @@ __global__ void __launch_bounds__(128, LGS_PREBWD_MIN_BLOCKS) preprocess_bwd(Pre
             sh_basis_grad<DEG>(d0, d1, d2, Y, dY);
             float gd[3] = {0.f, 0.f, 0.f};
             const float* shp = p.sh + i * NK * 3;
+            // coefficient k: dL/dsh_k = Y_k g (masked), and its colour
+            // <sh_k, g> times dY_k/d(dir) into the direction gradient
+            auto coef = [&](int k, float s0, float s1, float s2) {
+                dsh[k * 3 + 0] += Y[k] * gm[0];
+                dsh[k * 3 + 1] += Y[k] * gm[1];
+                dsh[k * 3 + 2] += Y[k] * gm[2];
+                const float ck = s0 * gm[0] + s1 * gm[1] + s2 * gm[2];
+                gd[0] += ck * dY[k][0];
+                gd[1] += ck * dY[k][1];
+                gd[2] += ck * dY[k][2];
+            };
+            if constexpr (NK % 4 == 0) {
+                // four coefficients (12 floats) per three 16-B loads
+                const float4* s4 = reinterpret_cast<const float4*>(shp);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                if (fl & (1u << ch)) continue;
-                const float gcc = gcol[ch];
-#pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    dsh[k * 3 + ch] += Y[k] * gcc;
-                    const float shv = shp[k * 3 + ch] * gcc;
-                    gd[0] += shv * dY[k][0];
-                    gd[1] += shv * dY[k][1];
-                    gd[2] += shv * dY[k][2];
+                for (int g4 = 0; g4 < NK / 4; ++g4) {
+                    const float4 u0 = s4[3 * g4], u1 = s4[3 * g4 + 1], u2 = s4[3 * g4 + 2];
+                    coef(4 * g4 + 0, u0.x, u0.y, u0.z);
+                    coef(4 * g4 + 1, u0.w, u1.x, u1.y);
+                    coef(4 * g4 + 2, u1.z, u1.w, u2.x);
+                    coef(4 * g4 + 3, u2.y, u2.z, u2.w);
                 }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NK; ++k) coef(k, shp[3 * k], shp[3 * k + 1], shp[3 * k + 2]);
             }
             const float pr = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
             dmu[0] += (gd[0] - d0 * pr) * id;
@@ -904,6 +923,7 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
         !grads->quats || !grads->opacities || !grads->sh)
         return LGS_ERR_ARG;
     if (!aligned16(g->quats)) return LGS_ERR_ALIGN;
+    if ((g->sh_degree == 1 || g->sh_degree == 3) && !aligned16(g->sh)) return LGS_ERR_ALIGN;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t m = g->n * (int64_t)n_views;
     if (cudaMemsetAsync(grads->xy2d, 0, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess ||
