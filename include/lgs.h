@@ -199,9 +199,10 @@ typedef struct {
     uint32_t* emit;
 } lgs_pre_out;
 
-/* Gradients (device, caller-zeroed, accumulated with atomics).
- * means [N,3], scales [N,3], quats [N,4], opacities [N], sh [N,(d+1)^2,3].
- * The *_2d buffers are per-(view, Gaussian) scratch gradients of the render
+/* Gradients (device, caller-zeroed; the per-Gaussian ones are added to, the
+ * per-entry scratch ones accumulated with atomics).
+ * means [N,3], scales [N,3], quats [N,4] (16-B aligned), opacities [N],
+ * sh [N,(d+1)^2,3] (16-B aligned for d = 1 and 3). The *_2d buffers are per-(view, Gaussian) scratch gradients of the render
  * stage, M = n_views*N entries: xy2d [M,2] (8-B aligned), conic2d [M,4] (a, b, c, o;
  * 16-B aligned), rgb2d [M,4] (r, g, b, unused; 16-B aligned); otherwise
  * lgs_render_bwd returns LGS_ERR_ALIGN. */

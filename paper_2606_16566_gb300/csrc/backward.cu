@@ -148,29 +148,29 @@ __device__ __forceinline__ void reduce_rows(const BwdRed& R, int ns, float (*sG)
     float yk[PPL];
 #pragma unroll
     for (int k = 0; k < PPL; ++k) yk[k] = (float)(by * WY + (8 * q) / WX + k * (WY / 2)) - 0.5f * (TH - 1);
+    using P = Px<PPL>;
     float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (e < ns) {
-        float S0[PPL], S1[PPL], S2[PPL];
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) S0[k] = S1[k] = S2[k] = 0.f;
-        float W0 = 0.f, W1 = 0.f, W2 = 0.f;
+        // per pixel row k of the lane's pixels (packed two-wide when PPL = 2)
+        P S0 = bcast<PPL>(0.f), S1 = S0, S2 = S0;
+        float2 W01 = make_float2(0.f, 0.f);
+        float W2 = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int col = 8 * q + (i ^ e);
             const float4 r4 = R.R4[e][col];
             const float w2 = R.R1[e][col];
             const float u = (float)i - 3.5f;
-            const float dpk[2] = {r4.x, r4.y};
-#pragma unroll
-            for (int k = 0; k < PPL; ++k) {
-                S0[k] += dpk[k];
-                S1[k] = fmaf(dpk[k], u, S1[k]);
-                S2[k] = fmaf(dpk[k], u * u, S2[k]);
-            }
-            W0 += r4.z;
-            W1 += r4.w;
+            P dp;
+            dp[0] = r4.x;
+            if (PPL == 2) dp[PPL - 1] = r4.y;
+            S0 = padd(S0, dp);
+            S1 = pfma(dp, bcast<PPL>(u), S1);
+            S2 = pfma(dp, bcast<PPL>(u * u), S2);
+            W01 = __fadd2_rn(W01, make_float2(r4.z, r4.w));
             W2 += w2;
         }
+        const float W0 = W01.x, W1 = W01.y;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
             const float Sx = fmaf(xc, S0[k], S1[k]);
@@ -687,9 +687,13 @@ __global__ void __launch_bounds__(128, LGS_PREBWD_MIN_BLOCKS) preprocess_bwd(Pre
     for (int k = 0; k < NK * 3; ++k) dsh[k] = 0.f;
     bool any = false;
 
+    // the next view's tile count is loaded one view ahead
+    uint32_t tiles_next = p.tiles[i];
     for (int v = 0; v < vs.n; ++v) {
         const int64_t m = (int64_t)v * N + i;
-        if (p.tiles[m] == 0) continue;
+        const uint32_t tiles_v = tiles_next;
+        if (v + 1 < vs.n) tiles_next = p.tiles[m + N];
+        if (tiles_v == 0) continue;
         any = true;
         const ViewRec& c = vs.v[v];
         // the per-entry scratch gradients: xy2d rows 8-B aligned, conic2d and
@@ -836,17 +840,36 @@ __global__ void __launch_bounds__(128, LGS_PREBWD_MIN_BLOCKS) preprocess_bwd(Pre
                              y * dR[5] + x * dR[6] + y * dR[7]);
     const float pr = w * dw + x * dx_ + y * dy_ + z * dz_;
     const float iq = 1.f / qn;
-    p.d_quats[4 * i + 0] += (dw - w * pr) * iq;
-    p.d_quats[4 * i + 1] += (dx_ - x * pr) * iq;
-    p.d_quats[4 * i + 2] += (dy_ - y * pr) * iq;
-    p.d_quats[4 * i + 3] += (dz_ - z * pr) * iq;
+    // each Gaussian's gradients belong to this thread alone: plain
+    // read-modify-writes, 16 B at a time where the rows are 16-B aligned
+    // (quats and SH of degree 1 and 3, checked on the host)
+    float4* dq = reinterpret_cast<float4*>(p.d_quats) + i;
+    float4 q = *dq;
+    q.x += (dw - w * pr) * iq;
+    q.y += (dx_ - x * pr) * iq;
+    q.z += (dy_ - y * pr) * iq;
+    q.w += (dz_ - z * pr) * iq;
+    *dq = q;
     p.d_means[3 * i + 0] += dmu[0];
     p.d_means[3 * i + 1] += dmu[1];
     p.d_means[3 * i + 2] += dmu[2];
     p.d_opac[i] += dop;
     float* dsp = p.d_sh + i * NK * 3;
+    if constexpr (NK % 4 == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dsp);
 #pragma unroll
-    for (int k = 0; k < NK * 3; ++k) dsp[k] += dsh[k];
+        for (int k = 0; k < NK * 3 / 4; ++k) {
+            float4 t = d4[k];
+            t.x += dsh[4 * k];
+            t.y += dsh[4 * k + 1];
+            t.z += dsh[4 * k + 2];
+            t.w += dsh[4 * k + 3];
+            d4[k] = t;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NK * 3; ++k) dsp[k] += dsh[k];
+    }
 }
 
 template <int TW, int TH, int WX, int WY>
@@ -922,8 +945,9 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     if (!g->means || !g->scales || !g->quats || !g->sh || !grads->means || !grads->scales ||
         !grads->quats || !grads->opacities || !grads->sh)
         return LGS_ERR_ARG;
-    if (!aligned16(g->quats)) return LGS_ERR_ALIGN;
-    if ((g->sh_degree == 1 || g->sh_degree == 3) && !aligned16(g->sh)) return LGS_ERR_ALIGN;
+    if (!aligned16(g->quats) || !aligned16(grads->quats)) return LGS_ERR_ALIGN;
+    if ((g->sh_degree == 1 || g->sh_degree == 3) && (!aligned16(g->sh) || !aligned16(grads->sh)))
+        return LGS_ERR_ALIGN;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t m = g->n * (int64_t)n_views;
     if (cudaMemsetAsync(grads->xy2d, 0, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess ||

@@ -466,17 +466,28 @@ __global__ void __launch_bounds__(256) emit_pairs_tight(const uint32_t* order, c
             uint32_t k = 0;
             if (e < items) k = (uint32_t)tight_tile_rows(ot, (int)tx * TW, TW, TH, oy0, oy1, &rlo, &rhi);
             const uint32_t ik = warp_inclusive_sum(k);
-            const uint32_t pos = run + ik - k;
-            for (uint32_t r = 0; r < k; ++r) {
-                const uint32_t q = pos + r;
-                const uint32_t tile = otoff + ((uint32_t)rlo + r) * ogx + tx;
-                if (q < total && LGS_CHECK((int64_t)start + q < capacity, 4, status) &&
-                    LGS_CHECK(tile < vs.n_tiles, 5, status) && LGS_CHECK(oent < (uint64_t)m, 6, status)) {
-                    tkey[start + q] = (KT)tile;
-                    tval[start + q] = oent;
+            const uint32_t rtot = __shfl_sync(0xffffffffu, ik, 31);
+            // the round's rtot instances (column after column, rows ascending)
+            // are written by consecutive lanes: output q belongs to the lane
+            // whose inclusive row count first exceeds q, so the stores of a
+            // warp are contiguous instead of strided by the columns' heights
+            const uint32_t tfirst = otoff + (uint32_t)rlo * ogx + tx;   // tile of the column's first row
+            for (uint32_t q0 = 0; q0 < rtot; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const int ow = owner_lane(ik, q);
+                const uint32_t qb = __shfl_sync(0xffffffffu, ik - k, ow);
+                const uint32_t tb = __shfl_sync(0xffffffffu, tfirst, ow);
+                const uint32_t tg = __shfl_sync(0xffffffffu, ogx, ow);
+                const uint32_t te = __shfl_sync(0xffffffffu, oent, ow);
+                const uint32_t pos = run + q;
+                const uint32_t tile = tb + (q - qb) * tg;
+                if (q < rtot && pos < total && LGS_CHECK((int64_t)start + pos < capacity, 4, status) &&
+                    LGS_CHECK(tile < vs.n_tiles, 5, status) && LGS_CHECK(te < (uint64_t)m, 6, status)) {
+                    tkey[start + pos] = (KT)tile;
+                    tval[start + pos] = te;
                 }
             }
-            run += __shfl_sync(0xffffffffu, ik, 31);
+            run += rtot;
         }
         if (run != total) {
             for (uint32_t q = run + lane; q < total; q += 32) {

@@ -148,3 +148,20 @@ def test_device_status_query_checks_its_arguments():
     code = ctypes.c_int32(7)
     assert lib.lgs_get_device_status(None, None, ctypes.byref(code), None) == L.LGS_ERR_ARG
     assert code.value == 7
+
+
+def test_misaligned_parameter_gradients_are_a_host_error():
+    # the preprocess adjoint adds to quats and (SH degree 1 and 3) SH
+    # gradients 16 B at a time: misaligned rows return before any launch
+    lib = L.load()
+    cam = (L.lgs_camera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 64, 48, 50.0, 50.0
+    cfg = L.lgs_config(16, 16, 0, 0, 0)
+    fake = ctypes.c_void_p(256)
+    pre = L.lgs_pre_out(*([256] * 8))
+    for deg, bad in ((3, "quats"), (3, "sh"), (1, "sh")):
+        g = L.lgs_gaussians(10, deg, 256, 256, 256, 256, 256)
+        gr = L.lgs_grads(*([256] * 8))
+        setattr(gr, bad, 260)
+        assert lib.lgs_render_bwd(ctypes.byref(g), cam, 1, ctypes.byref(cfg), ctypes.byref(pre), fake, fake,
+                                  fake, fake, fake, None, ctypes.byref(gr), fake, None) == L.LGS_ERR_ALIGN
