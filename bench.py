@@ -674,6 +674,15 @@ def run_ours(args, rank, world):
     cfg_l = variants[head]
     loaded = loaded_clock_mhz()
     probe_mhz = peaks["sm_mhz"] or 2070.0
+    # issue roofline: the 16 per-pixel operations the definition needs per
+    # pair (5 FMA power, ex2, clamp, 1/255 test, T(1 - alpha), stop test, w,
+    # 3 FMA colour, T update, contributor index) against 32 lanes x one warp
+    # instruction per scheduler per clock (4 schedulers per SM) at the probe clock
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = n_sm * 4 * 32 * probe_mhz * 1e6 / 1e12
+    issue = {"ops_per_pair": 16, "achieved": pairs * 16.0 / (render_ms * 1e-3) / 1e12, "peak": issue_peak,
+             "unit": "T lane-ops/s", "frac": pairs * 16.0 / (render_ms * 1e-3) / 1e12 / issue_peak,
+             "peak_basis": f"{n_sm} SMs x 4 schedulers x 32 lanes x {probe_mhz:.0f} MHz"}
 
     def summary(name):
         f = np.median(fwd[name], 0)
@@ -810,7 +819,8 @@ def run_ours(args, rank, world):
                      "peak_at_loaded_clock": peak * loaded / probe_mhz if loaded else None,
                      "loaded_clock_mhz": loaded,
                      "sfu": {"achieved": sfu_rate, "peak": peaks["ex2_tops"], "unit": "T ex2/s",
-                             "frac": sfu_rate / peaks["ex2_tops"]}},
+                             "frac": sfu_rate / peaks["ex2_tops"]},
+                     "issue": issue},
         "comparison": {
             "localgs_fwd_frames_s": fps, "plain_fwd_frames_s": s_plain["frames_s"],
             "fwd_ratio": s_plain["ms_per_step"] / ms_l,
