@@ -43,6 +43,35 @@ def test_preprocess_matches_oracle(seed, deg):
     assert rep["conic_max_rel"] < 1e-4, rep
 
 
+def test_preprocess_frustum_edge_entries_keep_their_rects():
+    """Gaussians scattered well beyond the view frustum with large, anisotropic
+    footprints: entries whose projected mean lies outside the image but whose
+    rect still reaches it must keep exactly the oracle's radius, tiles and
+    rect (the preprocess skips the projection only for entries that cannot
+    reach the tile grid)."""
+    n = 4000
+    sc, cams = scenes.random_small(n, seed=21, width=160, height=120, sh_degree=0, extent=4.0,
+                                   log_scale_mean=-2.5, log_scale_std=0.8, dist=3.0)
+    res = _render(sc, cams)
+    torch.cuda.synchronize()
+    g = gpu_pre_numpy(res["pre"], n)
+    o = oracle.preprocess(sc, cams[0])
+    rep = compare_preprocess(g, o, guard_gaussians(o))
+    print(rep)
+    assert rep["radius_mismatch"] == 0 and rep["tiles_mismatch"] == 0, rep
+    assert rep["rect_mismatch"] == 0 and rep["depth_mismatch"] == 0, rep
+    # both sides of the test are exercised: entries in front of the near plane
+    # whose projected mean lies off the image, kept (rect reaches in) and culled
+    c = cams[0]
+    V = np.asarray(c["viewmat"], np.float64)
+    t = sc["means"].astype(np.float64) @ V[:3, :3].T + V[:3, 3]
+    u = c["fx"] * t[:, 0] / t[:, 2] + c["cx"]
+    v = c["fy"] * t[:, 1] / t[:, 2] + c["cy"]
+    off_image = (t[:, 2] > 0.2) & ((u < 0) | (u >= 160) | (v < 0) | (v >= 120))
+    assert int(np.sum(off_image & (o["tiles"] > 0))) >= 200
+    assert int(np.sum(off_image & (o["tiles"] == 0))) >= 1000
+
+
 def test_preprocess_culls_and_counts_nonfinite():
     sc, cams = scenes.random_small(64, seed=5)
     clean = _render(sc, cams)["pre"].tiles.cpu().numpy()
