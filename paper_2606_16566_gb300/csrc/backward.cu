@@ -36,8 +36,10 @@
 
 namespace lgs {
 
+// Gaussians staged per round of the adjoint: 128 and 256 measured within
+// 0.5 % of each other (128 ahead), 128 halves the staging arrays.
 #ifndef LGS_BWD_BATCH
-#define LGS_BWD_BATCH 256
+#define LGS_BWD_BATCH 128
 #endif
 constexpr int BWD_BATCH = LGS_BWD_BATCH;
 constexpr float LOG2E_B = 1.4426950408889634f;
