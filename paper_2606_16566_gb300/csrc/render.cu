@@ -271,7 +271,7 @@ __device__ __forceinline__ void localgs_tile(const RenderParams& p, const Views&
             // walk it; the warp leaves once every lane is done (tested per 32)
             for (int i0 = 0; i0 < nl && !warp_done; i0 += 32) {
                 const int iend = min(nl, i0 + 32);
-#pragma unroll 4
+#pragma unroll 8
                 for (int i = i0; i < iend; ++i) {
                     const int off = sL[i];
                     if (VAR == VAR_LITERAL) {
