@@ -141,25 +141,45 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep(const uint32_t* t
     __shared__ uint32_t ws[32];
     m = pass_count(mv, m);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    // blocked arrangement: thread t owns items [t*ITEMS, (t+1)*ITEMS) of the block
+    // blocked arrangement: thread t owns items [t*ITEMS, (t+1)*ITEMS) of the
+    // block, loaded 16 B at a time where they all lie below the count (the
+    // block starts on a 2048-element boundary of a 256-B aligned buffer)
+    static_assert(SCAN_ITEMS % 4 == 0, "whole 16-B groups per thread");
     uint32_t v[SCAN_ITEMS];
     uint32_t s = 0;
+    const int64_t first = base + (int64_t)threadIdx.x * SCAN_ITEMS;
+    if (first + SCAN_ITEMS <= m) {
+        const uint4* t4 = reinterpret_cast<const uint4*>(tiles + first);
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
-        v[k] = i < m ? tiles[i] : 0u;
-        s += v[k];
+        for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+            const uint4 w = t4[q];
+            v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = first + k < m ? tiles[first + k] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) s += v[k];
     uint32_t tot;
     uint32_t ex = block_exclusive_scan<SCAN_THREADS>(s, ws, tot);
     // per block K may exceed 2^32 only if the capacity check fails; offsets wrap
     // harmlessly then because emission is skipped.
     uint32_t run = (uint32_t)block_sums[blockIdx.x] + ex;
+    uint32_t o[SCAN_ITEMS];
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
-        if (i < m) offsets[i] = run;
+        o[k] = run;
         run += v[k];
+    }
+    if (first + SCAN_ITEMS <= m) {
+        uint4* o4 = reinterpret_cast<uint4*>(offsets + first);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / 4; ++q) o4[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k)
+            if (first + k < m) offsets[first + k] = o[k];
     }
 }
 
