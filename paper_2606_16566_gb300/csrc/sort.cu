@@ -812,11 +812,12 @@ __global__ void __launch_bounds__(OS_THREADS, 2) onesweep_pass(
 // ------------------------------------------------------------------ radix passes (reduce-then-scan)
 // The same stable LSD pass as onesweep_pass, split so that no block ever waits
 // on another: rs_upsweep counts each 4096-element block's digits into a
-// digit-major table counts[d * nb + b]; rs_scan turns every row d into the
-// global output position of block b's first element of digit d (an exclusive
-// scan along the row plus the digit's base from the histogram kernels); and
-// rs_downsweep ranks its block's keys stably (the warp-ballot ranking of
-// onesweep_pass) and scatters them to those positions. The keys are read twice
+// digit-major table counts[d * nb + b]; rs_scan turns every row d into an
+// exclusive scan along the blocks and stores the row's total (the pass's count
+// of digit d); and rs_downsweep adds each digit's base (the exclusive scan of
+// the 256 totals), ranks its block's keys stably (the warp-ballot ranking of
+// onesweep_pass) and scatters them to those positions, so no histogram kernel
+// runs before the passes. The keys are read twice
 // (4 B per element more traffic than onesweep), but every kernel runs fully
 // parallel instead of along a look-back chain. Keys are u32 or, for tile ids
 // of at most 2^16 tiles, u16.
