@@ -149,7 +149,7 @@ typedef struct {
  * LGS_ERR_UNSUPPORTED for them).
  * batch = Gaussians the Local-GS render (LGS_MODE_LOCALGS) stages in shared
  * memory per round: 0 (= 256), 64, 128 or 256, else LGS_ERR_UNSUPPORTED; the
- * results do not depend on it. The other modes and the adjoint stage 256.
+ * results do not depend on it. The other render modes stage 256, the adjoint 128.
  * warp_w x warp_h = the pixel block one warp of the Local-GS render owns, with
  * its own bit of the culling mask (Sec. III-C3; the paper's layout, and the
  * default 0 x 0, is eight full-width strips of tile_h/8 rows). Blocks of 32
