@@ -950,6 +950,15 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     if (!aligned16(g->quats) || !aligned16(grads->quats)) return LGS_ERR_ALIGN;
     if ((g->sh_degree == 1 || g->sh_degree == 3) && (!aligned16(g->sh) || !aligned16(grads->sh)))
         return LGS_ERR_ALIGN;
+    // every host-checkable error returns before anything is enqueued
+    if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
+    const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
+    if (persistent && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
+    int wx = 0, wy = 0;
+    if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
+    if (cfg->mode != LGS_MODE_LOCALGS &&
+        (split_tile(cfg->tile_w, cfg->tile_h) || wx != cfg->tile_w || wy != cfg->tile_h / 8))
+        return LGS_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t m = g->n * (int64_t)n_views;
     if (cudaMemsetAsync(grads->xy2d, 0, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess ||
@@ -970,14 +979,6 @@ extern "C" lgs_status lgs_render_bwd(const lgs_gaussians* g, const lgs_camera* c
     bp.g_conic = grads->conic2d;
     bp.g_rgb = grads->rgb2d;
     bp.status = d_status;
-    if (cfg->mode != LGS_MODE_LOCALGS && cfg->mode != LGS_MODE_PLAIN) return LGS_ERR_UNSUPPORTED;
-    const bool persistent = (cfg->flags & LGS_FLAG_PERSISTENT) != 0;
-    if (persistent && cfg->mode != LGS_MODE_LOCALGS) return LGS_ERR_UNSUPPORTED;
-    int wx = 0, wy = 0;
-    if (!warp_block(cfg, &wx, &wy)) return LGS_ERR_UNSUPPORTED;
-    if (cfg->mode != LGS_MODE_LOCALGS &&
-        (split_tile(cfg->tile_w, cfg->tile_h) || wx != cfg->tile_w || wy != cfg->tile_h / 8))
-        return LGS_ERR_UNSUPPORTED;
     const int tw = cfg->tile_w, th = cfg->tile_h;
     if (tw == 16 && th == 16) st = launch_render_bwd<16, 16>(bp, vs, cfg->mode, wx, wy, persistent, s);
     else if (tw == 8 && th == 32) st = launch_render_bwd<8, 32>(bp, vs, cfg->mode, wx, wy, persistent, s);

@@ -165,3 +165,23 @@ def test_misaligned_parameter_gradients_are_a_host_error():
         setattr(gr, bad, 260)
         assert lib.lgs_render_bwd(ctypes.byref(g), cam, 1, ctypes.byref(cfg), ctypes.byref(pre), fake, fake,
                                   fake, fake, fake, None, ctypes.byref(gr), fake, None) == L.LGS_ERR_ALIGN
+
+
+def test_unsupported_warp_blocks_are_host_errors():
+    # the warp-block check runs on the host before any launch, for the forward
+    # and the adjoint: blocks outside the supported set, and other than 8x8 for
+    # the large (split) tiles, return LGS_ERR_UNSUPPORTED
+    lib = L.load()
+    cam = (L.lgs_camera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 64, 48, 50.0, 50.0
+    fake = ctypes.c_void_p(256)
+    pre = L.lgs_pre_out(*([256] * 8))
+    g = L.lgs_gaussians(10, 3, 256, 256, 256, 256, 256)
+    gr = L.lgs_grads(*([256] * 8))
+    for tile, block in (((16, 16), (4, 8)), ((16, 16), (8, 16)), ((8, 32), (16, 4)), ((32, 32), (16, 4)),
+                        ((32, 16), (16, 2)), ((32, 8), (16, 4))):
+        cfg = L.lgs_config(tile[0], tile[1], 0, 0, 0, block[0], block[1])
+        assert lib.lgs_render_fwd(ctypes.byref(pre), fake, fake, cam, 1, ctypes.byref(cfg), fake, fake, fake,
+                                  fake, None) == L.LGS_ERR_UNSUPPORTED, (tile, block)
+        assert lib.lgs_render_bwd(ctypes.byref(g), cam, 1, ctypes.byref(cfg), ctypes.byref(pre), fake, fake, fake,
+                                  fake, fake, None, ctypes.byref(gr), fake, None) == L.LGS_ERR_UNSUPPORTED, (tile, block)
